@@ -1,0 +1,361 @@
+"""Pins for the FP64 oracle: each test checks it against something other than
+itself -- the dense definition of A*x, brute force on tiny inputs, closed forms of
+the 27-point stencil, exact rational CG, and textbook CG properties. CPU only."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+
+U = 2.0 ** -53  # unit roundoff, FP64
+
+
+def dense_of(nrows, ncols, rows, cols, vals):
+    """Dense matrix with duplicates summed (the definition, via numpy scatter-add)."""
+    D = np.zeros((nrows, ncols))
+    np.add.at(D, (rows, cols), vals)
+    return D
+
+
+def assert_spmv_close(y, D, x, k_max):
+    """|y - D x| <= tol * (|D| |x|), tol = max(1e-13, 2 (k+2) u) for rows of <= k terms:
+    any two summation orders of k products each lie within gamma_k |D||x| of the exact sum."""
+    ref = D @ x
+    scale = np.abs(D) @ np.abs(x)
+    tol = max(1e-13, 2 * (k_max + 2) * U)
+    assert np.all(np.abs(y - ref) <= tol * scale + 1e-300), np.max(np.abs(y - ref) - tol * scale)
+
+
+SMALL_CASES = [
+    # (nrows, ncols, nnz, seed, dup_frac, empty_rows)
+    (1, 1, 1, 0, 0.0, 0),
+    (1, 1, 3, 1, 0.6, 0),
+    (5, 5, 11, 2, 0.0, 0),
+    (7, 13, 30, 3, 0.2, 2),
+    (13, 7, 30, 4, 0.2, 3),
+    (33, 33, 200, 5, 0.1, 4),
+    (64, 64, 700, 6, 0.3, 9),
+    (64, 64, 4096, 7, 0.0, 0),
+    (40, 64, 0, 8, 0.0, 0),
+    (64, 17, 64 * 17, 9, 0.5, 0),
+]
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_spmv_matches_dense_brute_force(orc, case):
+    nrows, ncols, nnz, seed, dup, empty = case
+    r, c, v = synth.random_coo(nrows, ncols, nnz, seed, dup_frac=dup, empty_rows=empty)
+    D = dense_of(nrows, ncols, r, c, v)
+    x = synth.uniform_x(ncols, seed) * 2 - 1
+    A = orc.canonicalize(nrows, ncols, r, c, v)
+    kmax = max(int(np.bincount(r, minlength=1).max()) if nnz else 0, 1)
+    assert_spmv_close(orc.spmv(A, x), D, x, kmax)
+    C = orc.coo_to_csr(A)
+    assert_spmv_close(orc.spmv(C, x), D, x, kmax)
+    if nrows == ncols:
+        Dg = orc.coo_to_dia(A)
+        assert_spmv_close(orc.spmv(Dg, x), D, x, kmax)
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_canonical_coo_brute_force(orc, case):
+    """Sorted unique (row, col); each value is the input-order left-to-right sum of its
+    duplicates (Python floats are IEEE FP64, so this is exact)."""
+    nrows, ncols, nnz, seed, dup, empty = case
+    r, c, v = synth.random_coo(nrows, ncols, nnz, seed, dup_frac=dup, empty_rows=empty)
+    acc = {}
+    for ri, ci, vi in zip(r.tolist(), c.tolist(), v.tolist()):
+        acc[(ri, ci)] = acc[(ri, ci)] + vi if (ri, ci) in acc else vi
+    keys = sorted(acc)
+    A = orc.canonicalize(nrows, ncols, r, c, v)
+    assert A.nnz == len(keys)
+    assert [(int(a), int(b)) for a, b in zip(A.ai, A.aj)] == keys
+    assert A.av.tolist() == [acc[k] for k in keys]
+
+
+def test_canonicalize_rejects_out_of_range(orc):
+    with pytest.raises(ValueError):
+        orc.canonicalize(3, 3, np.array([0, 3]), np.array([0, 0]), np.array([1.0, 2.0]))
+    with pytest.raises(ValueError):
+        orc.canonicalize(3, 3, np.array([0, 1]), np.array([-1, 0]), np.array([1.0, 2.0]))
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_csr_structure_and_round_trip(orc, case):
+    nrows, ncols, nnz, seed, dup, empty = case
+    r, c, v = synth.random_coo(nrows, ncols, nnz, seed, dup_frac=dup, empty_rows=empty)
+    A = orc.canonicalize(nrows, ncols, r, c, v)
+    C = orc.coo_to_csr(A)
+    assert C.irp[0] == 0 and C.irp[-1] == A.nnz
+    assert np.all(np.diff(C.irp) >= 0)
+    assert np.array_equal(np.diff(C.irp), np.bincount(A.ai, minlength=nrows)[:nrows])
+    B = orc.csr_to_coo(C)
+    assert np.array_equal(B.ai, A.ai) and np.array_equal(B.aj, A.aj)
+    assert np.array_equal(B.av, A.av)
+
+
+@pytest.mark.parametrize("case", [c for c in SMALL_CASES if c[0] == c[1]])
+def test_dia_structure_and_round_trip(orc, case):
+    nrows, ncols, nnz, seed, dup, empty = case
+    r, c, v = synth.random_coo(nrows, ncols, nnz, seed, dup_frac=dup, empty_rows=empty)
+    A = orc.canonicalize(nrows, ncols, r, c, v)
+    D = dense_of(nrows, ncols, A.ai, A.aj, A.av)
+    G = orc.coo_to_dia(A)
+    n = nrows
+    assert G.npad % 32 == 0 and n <= G.npad < n + 32
+    assert np.array_equal(G.doff, np.unique(A.aj.astype(np.int64) - A.ai))
+    AV = G.av.reshape(G.ndiags, G.npad)
+    for j, off in enumerate(G.doff.tolist()):
+        for i in range(G.npad):
+            k = i + off
+            want = D[i, k] if (i < n and 0 <= k < n) else 0.0
+            assert AV[j, i] == want
+    # round trip on entries without explicit zeros (DIA cannot tell a zero from padding)
+    keep = A.av != 0.0
+    B = orc.dia_to_coo(G)
+    assert np.array_equal(B.ai, A.ai[keep]) and np.array_equal(B.aj, A.aj[keep])
+    assert np.array_equal(B.av, A.av[keep])
+
+
+def test_dia_drops_explicit_zeros(orc):
+    r = np.array([0, 1, 1, 2])
+    c = np.array([0, 1, 2, 0])
+    v = np.array([1.0, 0.0, 2.0, 3.0])
+    A = orc.canonicalize(3, 3, r, c, v)
+    assert A.nnz == 4  # COO keeps the explicit zero
+    B = orc.dia_to_coo(orc.coo_to_dia(A))
+    assert B.nnz == 3 and list(zip(B.ai.tolist(), B.aj.tolist())) == [(0, 0), (1, 2), (2, 0)]
+
+
+# ---------------------------------------------------------------------------
+# 27-point stencil closed forms
+# ---------------------------------------------------------------------------
+
+def sep3(x3):
+    """(T x T x T) x with T = tridiag(1, 1, 1): three independent 3-point passes."""
+    out = x3
+    for ax in range(3):
+        s = out.copy()
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax], hi[ax] = slice(0, -1), slice(1, None)
+        s[tuple(lo)] += out[tuple(hi)]
+        s[tuple(hi)] += out[tuple(lo)]
+        out = s
+    return out
+
+
+def stencil_apply_closed_form(g, x):
+    """A x with A = 27 I - T(x)T(x)T: diagonal 27 - 1 = 26, each neighbour -1."""
+    x3 = x.reshape(g, g, g)
+    return (27.0 * x3 - sep3(x3)).ravel(), (25.0 * np.abs(x3) + sep3(np.abs(x3))).ravel()
+
+
+@pytest.mark.parametrize("g", [2, 3, 5, 16, 24])
+def test_stencil_structure(orc, g):
+    r, c, v = synth.stencil27(g)
+    n = g ** 3
+    assert r.size == (3 * g - 2) ** 3
+    A = orc.canonicalize(n, n, r, c, v)
+    assert A.nnz == (3 * g - 2) ** 3
+    C = orc.coo_to_csr(A)
+    lens = np.diff(C.irp)
+    # a row's length is prod over the 3 axes of (2 at a face, 3 inside)
+    want = {}
+    for kb in range(4):  # number of axes on which the point sits on a face
+        from math import comb
+        length = 3 ** (3 - kb) * 2 ** kb
+        count = comb(3, kb) * (2 ** kb) * max(g - 2, 0) ** (3 - kb) if g > 1 else 0
+        want[length] = want.get(length, 0) + count
+    got = {int(k): int(cnt) for k, cnt in zip(*np.unique(lens, return_counts=True))}
+    assert got == {k: c for k, c in want.items() if c}
+    # b = A 1 has b_i = 27 - len_i exactly: interior rows sum to zero
+    b = orc.spmv(C, np.ones(n))
+    assert np.array_equal(b, 27.0 - lens)
+    G = orc.coo_to_dia(A)
+    offs = sorted({dz * g * g + dy * g + dx for dz in (-1, 0, 1) for dy in (-1, 0, 1)
+                   for dx in (-1, 0, 1)})
+    if g >= 3:
+        assert G.doff.tolist() == offs
+    assert np.count_nonzero(G.av) == A.nnz
+
+
+@pytest.mark.parametrize("g", [4, 16, 24])
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_stencil_spmv_matches_separable_closed_form(orc, g, fmt):
+    n = g ** 3
+    r, c, v = synth.stencil27(g)
+    A = orc.convert(orc.canonicalize(n, n, r, c, v), fmt)
+    x = synth.uniform_x(n, 0)
+    ref, scale = stencil_apply_closed_form(g, x)
+    y = orc.spmv(A, x)
+    assert np.all(np.abs(y - ref) <= 1e-13 * scale)
+
+
+def stencil_eigs(g):
+    """Eigenvalues of A = 27 I - T(x)T(x)T: T has eigenvalues 1 + 2 cos(k pi/(g+1))."""
+    t = 1.0 + 2.0 * np.cos(np.arange(1, g + 1) * np.pi / (g + 1))
+    return 27.0 - np.einsum("i,j,k->ijk", t, t, t).ravel()
+
+
+@pytest.mark.parametrize("g", [3, 5, 7])
+def test_stencil_eigenvalue_closed_form(orc, g):
+    n = g ** 3
+    r, c, v = synth.stencil27(g)
+    D = dense_of(n, n, r, c, v)
+    assert np.allclose(np.sort(stencil_eigs(g)), np.linalg.eigvalsh(D), atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# CG
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("g", [8, 16])
+@pytest.mark.parametrize("fmt", ["csr", "dia", "coo"])
+def test_cg_recovers_ones(orc, g, fmt):
+    n = g ** 3
+    r, c, v = synth.stencil27(g)
+    A = orc.convert(orc.canonicalize(n, n, r, c, v), fmt)
+    lam = stencil_eigs(g)
+    kappa = lam.max() / lam.min()
+    b = orc.spmv(A, np.ones(n))
+    x, st, k, rel, hist, aerr = orc.cg(A, b, tol=1e-10, maxit=2000, xstar=np.ones(n))
+    assert st == orc.OK
+    assert rel <= 1e-10 and hist[-1] == pytest.approx(rel)
+    # the textbook bound on iterations: sqrt(kappa)/2 * ln(2/eps) with eps the A-norm
+    # error reduction; eps <= tol / sqrt(kappa) suffices for the residual test
+    bound = int(np.ceil(np.sqrt(kappa) / 2 * np.log(2 * np.sqrt(kappa) / 1e-10)))
+    assert k <= bound
+    # forward error bounded by kappa times the relative residual
+    assert np.linalg.norm(x - 1) / np.sqrt(n) <= kappa * rel * 1.01
+    # A-norm error is monotonically non-increasing (rounding slack 1e-12 of its start)
+    assert np.all(np.diff(aerr) <= 1e-12 * aerr[0])
+    # true residual agrees with the recursive one
+    true = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+    assert true <= 2e-10
+
+
+def test_cg_diagonal_distinct_eigenvalues(orc):
+    """CG on an SPD matrix with m distinct eigenvalues ends in at most m iterations."""
+    for m in (1, 2, 3, 5, 8):
+        n = 200
+        eig = np.linspace(1.0, 10.0, m)
+        d = eig[np.arange(n) % m]
+        A = orc.canonicalize(n, n, np.arange(n), np.arange(n), d)
+        b = synth.uniform_x(n, m) + 0.5
+        x, st, k, rel, _, _ = orc.cg(A, b, tol=1e-12, maxit=50)
+        assert st == orc.OK and k <= m
+        assert np.allclose(x, b / d, rtol=1e-11)
+
+
+def _exact_cg(M, b, iters):
+    """CG in exact rational arithmetic (fractions), from x0 = 0."""
+    n = len(b)
+    x = [Fraction(0)] * n
+    r = list(b)
+    p = list(r)
+    rho = sum(ri * ri for ri in r)
+    out = []
+    for _ in range(iters):
+        q = [sum(M[i][j] * p[j] for j in range(n)) for i in range(n)]
+        alpha = rho / sum(p[i] * q[i] for i in range(n))
+        x = [x[i] + alpha * p[i] for i in range(n)]
+        r = [r[i] - alpha * q[i] for i in range(n)]
+        rho_new = sum(ri * ri for ri in r)
+        beta = rho_new / rho
+        rho = rho_new
+        p = [r[i] + beta * p[i] for i in range(n)]
+        out.append([float(t) for t in x])
+    return out
+
+
+def test_cg_iterates_match_exact_rational_cg(orc):
+    rng = np.random.default_rng(11)
+    n = 7
+    B = rng.integers(-3, 4, size=(n, n))
+    M = B @ B.T + n * np.eye(n, dtype=np.int64)  # SPD, integer
+    b = rng.integers(-5, 6, size=n)
+    exact = _exact_cg([[Fraction(int(t)) for t in row] for row in M],
+                      [Fraction(int(t)) for t in b], n - 1)
+    rows, cols = np.nonzero(M)
+    A = orc.canonicalize(n, n, rows, cols, M[rows, cols].astype(float))
+    for k in range(1, n):
+        x, st, it, _, _, _ = orc.cg(A, b.astype(float), tol=0.0, maxit=k)
+        assert st == orc.OK and it == k
+        assert np.allclose(x, exact[k - 1], rtol=1e-12, atol=1e-12)
+
+
+def test_cg_special_cases(orc):
+    n = 10
+    A = orc.canonicalize(n, n, np.arange(n), np.arange(n), np.arange(1.0, n + 1))
+    # b = 0 -> x = 0, zero iterations
+    x, st, k, rel, _, _ = orc.cg(A, np.zeros(n), x0=np.ones(n), tol=1e-10, maxit=5)
+    assert st == orc.OK and k == 0 and np.all(x == 0)
+    # too few iterations -> not converged, last iterate kept
+    x, st, k, rel, _, _ = orc.cg(A, np.ones(n), tol=1e-14, maxit=3)
+    assert st == orc.NOTCONV and k == 3 and rel > 1e-14
+    # tol <= 0 runs exactly maxit iterations and reports success
+    x, st, k, rel, _, _ = orc.cg(A, np.ones(n), tol=0.0, maxit=4)
+    assert st == orc.OK and k == 4
+    # indefinite matrix: p.Ap <= 0 is a breakdown
+    Aind = orc.canonicalize(2, 2, np.array([0, 1]), np.array([0, 1]), np.array([1.0, -1.0]))
+    x, st, k, rel, _, _ = orc.cg(Aind, np.array([1.0, 1.0]), tol=1e-10, maxit=10)
+    assert st == orc.BREAKDOWN and k == 0 and np.all(x == 0)
+    # already converged start
+    x, st, k, rel, _, _ = orc.cg(A, np.arange(1.0, n + 1), x0=np.ones(n), tol=1e-10, maxit=10)
+    assert st == orc.OK and k == 0
+
+
+# ---------------------------------------------------------------------------
+# storage rounding
+# ---------------------------------------------------------------------------
+
+def _bf16_by_bits(v):
+    """BF16 round-to-nearest-even from FP64 by integer arithmetic on the FP64 bits:
+    keep 7 explicit mantissa bits (45 bits dropped) and round the dropped part."""
+    out = []
+    for t in np.asarray(v, np.float64).tolist():
+        bits = np.array([t], np.float64).view(np.uint64)[0].item()
+        sign, rest = bits >> 63, bits & ((1 << 63) - 1)
+        drop = 52 - 7
+        low = rest & ((1 << drop) - 1)
+        kept = rest >> drop
+        half = 1 << (drop - 1)
+        if low > half or (low == half and (kept & 1)):
+            kept += 1
+        res = np.array([(sign << 63) | (kept << drop)], np.uint64).view(np.float64)[0]
+        out.append(float(res))
+    return np.array(out)
+
+
+def test_round_values(orc):
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.uniform(-4, 4, 5000), rng.normal(0, 1e3, 1000),
+                        [1.0, -1.0, 26.0, -26.0, 0.0, 1 + 2**-8, 1 + 3 * 2**-8,
+                         1 + 2**-8 + 2**-30, 3.0e38]])
+    assert np.array_equal(orc.round_values(v, "f32"), v.astype(np.float32).astype(np.float64))
+    bf = orc.round_values(v, "bf16")
+    assert np.array_equal(bf[:-1], _bf16_by_bits(v[:-1]))
+    # ties to even, and no double rounding through FP32
+    assert orc.round_values([1 + 2**-8], "bf16")[0] == 1.0
+    assert orc.round_values([1 + 3 * 2**-8], "bf16")[0] == 1 + 2**-6
+    assert orc.round_values([1 + 2**-8 + 2**-30], "bf16")[0] == 1 + 2**-7
+    assert np.isinf(orc.round_values([3.5e38], "bf16")[0])
+    # stencil values are exact in both
+    assert np.array_equal(orc.round_values([26.0, -1.0], "bf16"), [26.0, -1.0])
+
+
+def test_cg_ir_reaches_fp64_tolerance_with_bf16_values(orc):
+    g = 12
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 3)
+    A = orc.canonicalize(n, n, r, c, v)
+    C = orc.coo_to_csr(A)
+    Clo = orc.with_values(C, "bf16")
+    assert not np.array_equal(Clo.av, C.av)  # the rounding is exercised
+    b = orc.spmv(C, np.ones(n))
+    x, st, outer, inner, rel = orc.cg_ir(C, Clo, b, tol=1e-10, inner_tol=1e-3)
+    assert st == orc.OK and rel <= 1e-10 and outer >= 2
+    true = np.linalg.norm(b - orc.spmv(C, x)) / np.linalg.norm(b)
+    assert true <= 1e-10 and np.max(np.abs(x - 1)) < 1e-8
