@@ -1,0 +1,402 @@
+"""Benchmark: SpMV over COO / CSR / DIA and FP64 CG on the 27-point HPCG stencil.
+
+Workload (one "step", data resident in HBM): on the 128^3 stencil (n = 2,097,152,
+nnz = 55,742,968, FP64 values, int32 indices) one SpMV per format (COO, CSR, DIA)
+followed by 50 unpreconditioned FP64 CG iterations on the DIA matrix from x0 = 0 with
+b = A 1. Conversion (HPCG's optimisation set-up phase) is done once, untimed, and
+reported. Metric: GB/s by the algorithmic byte model (values + indices + x + y per
+SpMV; 88 n extra bytes per CG iteration for its vector passes); per-format GB/s, the
+DIA kernel against the HBM roofline, and CG time-to-1e-10 in FP64 and mixed precision
+(FP32 DIA values with FP64 refinement) are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mspv|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the
+path has no exchange step here); timing is the max over ranks after a barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "SpMV GB/s (% of HBM peak) per format; CG time-to-1e-10, FP64 vs mixed"
+GRID = 128
+CG_ITERS = 50
+NDIAGS = 27
+
+
+def byte_model(n: int, nnz: int, ndiags: int, vbytes: int = 8) -> dict:
+    """Algorithmic bytes of one SpMV per format and of one CG iteration (DIA)."""
+    coo = (vbytes + 8) * nnz + 16 * n
+    csr = (vbytes + 4) * nnz + 4 * (n + 1) + 16 * n
+    dia = vbytes * ndiags * n + 4 * ndiags + 16 * n
+    cg_iter = (dia - 16 * n) + 88 * n
+    return {"coo": coo, "csr": csr, "dia": dia, "cg_iter": cg_iter}
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_mspv(args, world, rank, local):
+    import torch
+    import paper_2304_09511_gb300 as mspv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    os.environ.setdefault("MSPV_CG_CHECK_EVERY", str(CG_ITERS))
+
+    g = args.grid
+    n = g ** 3
+    rows, cols, vals = synth.stencil27(g)
+    nnz = rows.size
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    A = mspv.Matrix.from_coo(n, n, torch.from_numpy(rows).to(dev), torch.from_numpy(cols).to(dev),
+                             torch.from_numpy(vals).to(dev))
+    torch.cuda.synchronize()
+    t_coo = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    C = A.convert("csr")
+    t_csr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    D = A.convert("dia")
+    t_dia = time.perf_counter() - t0
+    D32 = A.convert("dia", "f32")
+    del rows, cols, vals
+    ndiags = D.info["ndiags"]
+    bm = byte_model(n, nnz, ndiags)
+
+    x = torch.from_numpy(synth.uniform_x(n, 0)).to(dev)
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    b = D.spmv(ones)
+    y = {f: torch.empty(n, dtype=torch.float64, device=dev) for f in ("coo", "csr", "dia")}
+    xcg = torch.zeros(n, dtype=torch.float64, device=dev)
+    mats = {"coo": A, "csr": C, "dia": D}
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        for k, f in enumerate(("coo", "csr", "dia")):
+            mats[f].spmv(x, y[f])
+            if events:
+                events[k + 1].record(stream)
+        xcg.zero_()
+        D.cg(b, x=xcg, tol=0.0, maxit=args.cg_iters)
+        if events:
+            events[4].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(K):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = max_over_ranks(start.elapsed_time(end), world)
+
+    seg = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(K)])
+    ms = {"coo": float(seg[:, 0].mean()), "csr": float(seg[:, 1].mean()), "dia": float(seg[:, 2].mean()),
+          "cg": float(seg[:, 3].mean())}
+    cg_bytes = bm["cg_iter"] * args.cg_iters + bm["dia"] + 32 * n   # init: A x0, r = b - q, p = r
+    step_bytes = bm["coo"] + bm["csr"] + bm["dia"] + cg_bytes
+    ms_per_step = elapsed_ms / K
+    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
+    peaks = load_peaks()
+    per_format = {}
+    for f in ("coo", "csr", "dia"):
+        gbs = bm[f] / (ms[f] * 1e-3) / 1e9
+        per_format[f] = {"ms": round(ms[f], 5), "GB_s": round(gbs, 1),
+                         "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
+                         "frac_of_nominal_8TBs": round(gbs / 8000.0, 4),
+                         "GFLOP_s": round(2 * nnz / (ms[f] * 1e-3) / 1e9, 1),
+                         "bytes": bm[f]}
+    cg_ms_iter = ms["cg"] / args.cg_iters
+
+    # gpu launches of this library inside the timed region
+    coo_launches = 1 + (1 if (nnz + 255) // 256 > 1 else 0)
+    launches_per_step = coo_launches + 1 + 1 + (2 + 3 * args.cg_iters)
+
+    # end to end through the public API with host buffers: H2D of x and b, D2H of the
+    # three SpMV results and the CG solution, inside the timed region
+    x_h = torch.from_numpy(synth.uniform_x(n, 0)).pin_memory()
+    b_h = b.cpu().pin_memory()
+    outs_h = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
+    x_d = torch.empty_like(x)
+    b_d = torch.empty_like(b)
+
+    def e2e_step():
+        x_d.copy_(x_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        for i, f in enumerate(("coo", "csr", "dia")):
+            mats[f].spmv(x_d, y[f])
+            outs_h[i].copy_(y[f], non_blocking=True)
+        xcg.zero_()
+        D.cg(b_d, x=xcg, tol=0.0, maxit=args.cg_iters)
+        outs_h[3].copy_(xcg, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    s2 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for _ in range(K):
+        e2e_step()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(s2.elapsed_time(e2), world) / K
+    e2e_value = world * step_bytes / (e2e_ms * 1e-3) / 1e9
+
+    # CG time-to-1e-10 (FP64 DIA) and mixed precision (FP32 DIA values, FP64 refinement)
+    tt = {}
+    for label, fn in (("fp64", lambda xx: D.cg(b, x=xx, tol=1e-10, maxit=5000)),
+                      ("mixed_f32_ir", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=1e-5,
+                                                          max_outer=20, maxit_inner=5000))):
+        os.environ["MSPV_CG_CHECK_EVERY"] = "10"
+        xx = torch.zeros(n, dtype=torch.float64, device=dev)
+        fn(xx)   # warm
+        xx.zero_()
+        s3 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        s3.record(stream)
+        res = fn(xx)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        tt[label] = {"ms": round(s3.elapsed_time(e3), 3), "iters": res.iters, "outer": res.outer_iters,
+                     "relres": res.relres, "converged": res.converged}
+
+    dia_launch_ms = ms["dia"]
+    achieved = bm["dia"] / (dia_launch_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"27-point stencil {g}^3 (n={n}, nnz={nnz}), FP64 values, int32 indices; "
+                               f"step = SpMV COO + CSR + DIA, then {args.cg_iters} FP64 CG iterations (DIA)",
+                   "l2": "inputs larger than L2 (matrices 486-925 MB per format; no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "per_format": per_format,
+        "cg": {"ms_per_iter": round(cg_ms_iter, 5),
+               "GB_s": round(bm["cg_iter"] / (cg_ms_iter * 1e-3) / 1e9, 1),
+               "time_to_1e-10": tt},
+        "convert_s": {"coo_sort_coalesce": round(t_coo, 4), "csr": round(t_csr, 4), "dia": round(t_dia, 4)},
+        "roofline": {"kernel": "spmv_dia_kernel<double>", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": peaks["source"],
+                     "traffic": None, "bytes_per_launch": bm["dia"]},
+        "e2e": {"value": round(e2e_value, 1), "unit": "GB/s", "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 32 * n},
+        "gpu_launches": launches_per_step * K,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, args.cpu_cg_iters)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_workload(g):
+    import oracle
+    n = g ** 3
+    rows, cols, vals = synth.stencil27(g)
+    # the generator emits canonical COO already (sorted by (row, col), no duplicates)
+    O = oracle.Matrix(oracle.COO, n, n, rows.size, ai=rows, aj=cols, av=vals)
+    return oracle, n, {"coo": O, "csr": oracle.coo_to_csr(O), "dia": oracle.coo_to_dia(O)}
+
+
+def oracle_sample(oracle, n, mats, cg_iters):
+    """One bounded sample: one SpMV per format and `cg_iters` CG iterations (DIA)."""
+    x = synth.uniform_x(n, 0)
+    t = {}
+    for f in ("coo", "csr", "dia"):
+        t0 = time.perf_counter()
+        oracle.spmv(mats[f], x)
+        t[f] = time.perf_counter() - t0
+    b = oracle.spmv(mats["dia"], np.ones(n))
+    t0 = time.perf_counter()
+    oracle.cg(mats["dia"], b, tol=0.0, maxit=cg_iters)
+    t["cg"] = time.perf_counter() - t0
+    return t
+
+
+def cpu_baseline(g, cg_iters):
+    oracle, n, mats = oracle_workload(g)
+    nnz = mats["coo"].nnz
+    bm = byte_model(n, nnz, mats["dia"].ndiags)
+    t = oracle_sample(oracle, n, mats, cg_iters)
+    byts = bm["coo"] + bm["csr"] + bm["dia"] + bm["cg_iter"] * cg_iters + bm["dia"] + 32 * n
+    secs = sum(t.values())
+    return {"value": round(byts / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{g}^3 stencil: one SpMV per format + {cg_iters} CG iterations (DIA), serial C oracle",
+            "seconds": round(secs, 3),
+            "per_format_GB_s": {f: round(bm[f] / t[f] / 1e9, 3) for f in ("coo", "csr", "dia")}}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    oracle, n, mats = oracle_workload(args.grid)
+    nnz = mats["coo"].nnz
+    bm = byte_model(n, nnz, mats["dia"].ndiags)
+    byts = bm["coo"] + bm["csr"] + bm["dia"] + bm["cg_iter"] * args.cpu_cg_iters + bm["dia"] + 32 * n
+    for _ in range(args.warmup):
+        oracle_sample(oracle, n, mats, args.cpu_cg_iters)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(oracle, n, mats, args.cpu_cg_iters)
+    secs = time.perf_counter() - t0
+    value = byts * args.steps / secs / 1e9
+    sample = (f"{args.grid}^3 stencil: one SpMV per format + {args.cpu_cg_iters} CG iterations (DIA) "
+              "per step, serial C oracle")
+    return {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"27-point stencil {args.grid}^3 (n={n}, nnz={nnz}), FP64 values, int32 indices; "
+                                   "bounded sample of the GPU step (SpMV per format + CG iterations)",
+                       "parallelism": "cpu serial"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["mspv", "reference"], default="mspv")
+    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
+    ap.add_argument("--cpu-cg-iters", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mspv":
+        args.warmup = 3
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_mspv(args, world, rank, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * mspv — sparse matrix-vector multiply and conjugate gradient on GB300 (sm_103a).
+ *
+ * C ABI of libmspv.so. The operations follow the problem statement of
+ * "Morpheus unleashed: Fast cross-platform SpMV on emerging architectures"
+ * (arXiv 2304.09511): a sparse matrix held in one of the three storage formats of
+ * Sec. II-B (COO, CSR, DIA), the SpMV of Algorithms 1-3, and the unpreconditioned
+ * conjugate-gradient loop the paper runs in its HPCG experiments (Sec. VI, with the
+ * preconditioner disabled). The handle lifecycle mirrors the create -> optimise ->
+ * execute -> destroy sequence the paper describes for vendor sparse handles
+ * (Sec. III): mspv_create_coo / mspv_convert / mspv_spmv / mspv_destroy.
+ *
+ * Conventions (every entry point):
+ *  - Indices are 0-based int32. nnz is int64 but must stay below 2^31.
+ *  - Matrix values are given in FP64. A handle may store them as FP64, FP32 or
+ *    BF16 (mspv_value_type); arithmetic inside SpMV is always FP64 (values are
+ *    widened exactly before each multiply-add).
+ *  - Vectors passed to mspv_spmv / mspv_cg_* are DEVICE pointers to FP64 arrays,
+ *    owned by the caller, which must stay valid until the stream work completes.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. mspv_spmv is asynchronous on that stream. mspv_create_coo,
+ *    mspv_convert, mspv_export and the CG solvers synchronise the stream before
+ *    they return.
+ *  - Handles own device copies of everything they hold (inputs are copied in,
+ *    never aliased). A handle must not be used by two calls that overlap in time.
+ *  - No C++ exception crosses this boundary. Every call returns a status; the
+ *    calling thread's last error message is kept for mspv_last_error().
+ *  - Device faults are never used to signal errors: bounds, sizes and numerical
+ *    breakdown are detected and returned as statuses.
+ */
+#ifndef MSPV_H
+#define MSPV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MSPV_API __attribute__((visibility("default")))
+#else
+#define MSPV_API
+#endif
+
+typedef struct mspv_matrix* mspv_matrix_t;
+
+/* Storage formats of Sec. II-B. */
+typedef enum { MSPV_COO = 0, MSPV_CSR = 1, MSPV_DIA = 2 } mspv_format;
+
+/* Storage type of matrix values; accumulation is always FP64. */
+typedef enum { MSPV_F64 = 0, MSPV_F32 = 1, MSPV_BF16 = 2 } mspv_value_type;
+
+typedef enum {
+    MSPV_OK = 0,
+    MSPV_EINVAL = 1,      /* bad argument: null pointer, negative size, index out of range */
+    MSPV_ENOMEM = 2,      /* device allocation failed or exceeded MSPV_MAX_BYTES */
+    MSPV_ETOOBIG = 3,     /* DIA storage would exceed its fill cap, or nnz >= 2^31 */
+    MSPV_EFORMAT = 4,     /* operation not defined for this format (e.g. DIA of a non-square matrix) */
+    MSPV_ECUDA = 5,       /* a CUDA runtime call failed; see mspv_last_error() */
+    MSPV_ENOTCONV = 6,    /* CG reached its iteration limit above the tolerance */
+    MSPV_EBREAKDOWN = 7   /* CG found p.Ap <= 0 or a non-finite step (matrix not SPD) */
+} mspv_status;
+
+/* Description of a handle, filled by mspv_info. */
+typedef struct {
+    int32_t format;          /* mspv_format */
+    int32_t value_type;      /* mspv_value_type */
+    int32_t nrows, ncols;
+    int64_t nnz;             /* stored entries (COO/CSR); for DIA the entries it was built from */
+    int32_t ndiags;          /* DIA: number of stored diagonals, else 0 */
+    int32_t npad;            /* DIA: padded row count of each diagonal (multiple of 32), else 0 */
+    int32_t csr_vector;      /* CSR: lanes per row the SpMV kernel uses (1..32), else 0 */
+    int32_t row_max;         /* longest row */
+    double row_mean;         /* mean row length */
+    double row_std;          /* standard deviation of row lengths */
+    int64_t empty_rows;      /* rows with no stored entry */
+    int64_t device_bytes;    /* device memory the handle holds */
+} mspv_matrix_info;
+
+/*
+ * Create a COO handle from triplets (Sec. II-B-1: arrays AI, AJ, AV of length NNZ,
+ * in no particular order). rows/cols/vals are host pointers when on_device == 0,
+ * device pointers otherwise; they are read, never kept. The handle stores the
+ * canonical form: entries sorted by (row, col), stable, with duplicate (row, col)
+ * pairs summed in input order; explicit zeros are kept.
+ * Errors: EINVAL for nrows/ncols/nnz < 0, null arrays with nnz > 0, or any index
+ * outside [0, nrows) x [0, ncols); ETOOBIG for nnz >= 2^31; ENOMEM; ECUDA.
+ * On error *out is set to NULL.
+ */
+MSPV_API mspv_status mspv_create_coo(int32_t nrows, int32_t ncols, int64_t nnz,
+                                     const int32_t* rows, const int32_t* cols,
+                                     const double* vals, int on_device, void* stream,
+                                     mspv_matrix_t* out);
+
+/*
+ * Build a new handle holding A in format `format` with values stored as
+ * `value_type` (rounded to nearest even from FP64). A is not modified.
+ *  - CSR (Sec. II-B-2): IRP[nrows + 1] = exclusive scan of the row lengths, AJ and
+ *    AV in canonical order.
+ *  - DIA (Sec. II-B-3): DOFF = ascending distinct offsets col - row; AV is stored
+ *    diagonal-major, AV[j * npad + i] multiplying x[i + DOFF[j]], with
+ *    npad = ceil(nrows / 32) * 32 and zeros in every slot outside the matrix or
+ *    without an entry. Square matrices only (EFORMAT otherwise). ETOOBIG when
+ *    ndiags * npad exceeds max(32 * nnz, 2^20) slots (DIA's storage blow-up on
+ *    scattered patterns), or the MSPV_DIA_MAX_FILL override of the factor 32.
+ *  - COO: a copy, possibly with another value type.
+ * A may be COO or CSR; converting from DIA returns EFORMAT.
+ */
+MSPV_API mspv_status mspv_convert(mspv_matrix_t A, mspv_format format,
+                                  mspv_value_type value_type, void* stream,
+                                  mspv_matrix_t* out);
+
+/*
+ * y = A x (overwrite), by Algorithm 1 (COO), 2 (CSR) or 3 (DIA) for A's format.
+ * x has ncols entries, y has nrows entries; both are device FP64 arrays and must
+ * not overlap. Rows without entries get y = 0. Asynchronous on `stream`.
+ * Summation order inside a row differs from the sequential order of the
+ * algorithms (FP64 fused multiply-adds and tree reductions); results agree with
+ * the sequential sum within 2 (k + 2) u sum_j |a_ij x_j| for a row of k entries.
+ * Repeated calls on the same inputs give bit-identical y.
+ */
+MSPV_API mspv_status mspv_spmv(mspv_matrix_t A, const double* x, double* y, void* stream);
+
+/*
+ * Unpreconditioned conjugate gradient on A x = b (A square, assumed SPD), started
+ * from the x passed in and overwritten with the result:
+ *   r = b - A x, p = r, rho = r.r; per iteration q = A p, alpha = rho / p.q,
+ *   x += alpha p, r -= alpha q, rho' = r.r; stop when sqrt(rho') <= tol ||b||_2;
+ *   beta = rho' / rho, p = r + beta p.
+ * tol <= 0 runs exactly maxit iterations (earlier only if r becomes exactly 0)
+ * and returns OK. ||b|| = 0 sets x = 0 with zero iterations.
+ * Outputs (host pointers, may be NULL): *iters = iterations done, *relres =
+ * sqrt(rho) / ||b|| (the recursively updated residual).
+ * Returns OK, ENOTCONV (maxit reached with tol > 0; x holds the last iterate) or
+ * EBREAKDOWN (p.q <= 0 or non-finite alpha; x holds the last completed iterate).
+ * Vector work runs on the device with device-resident scalars; the host polls a
+ * convergence flag every MSPV_CG_CHECK_EVERY iterations (default 10); launches past
+ * convergence are no-ops, so results do not depend on that interval.
+ * Workspace (3 vectors + reduction partials) is allocated once per handle.
+ */
+MSPV_API mspv_status mspv_cg_solve(mspv_matrix_t A, const double* b, double* x, double tol,
+                                   int32_t maxit, void* stream, int32_t* iters,
+                                   double* relres);
+
+/*
+ * Mixed-precision CG with iterative refinement (not in the paper). A64 and Alo hold
+ * the same matrix; Alo typically stores FP32 or BF16 values (any format). Outer loop
+ * in FP64 on A64: r = b - A64 x; stop when ||r|| / ||b|| <= tol; otherwise solve
+ * Alo d = r by mspv_cg_solve's iteration from d = 0 to relative tolerance inner_tol
+ * (at most maxit_inner iterations), then x += d. At most max_outer corrections.
+ * Outputs (host, may be NULL): *outer_iters, *inner_iters (sum over corrections),
+ * *relres = final ||b - A64 x|| / ||b||. Returns OK, ENOTCONV or EBREAKDOWN.
+ */
+MSPV_API mspv_status mspv_cg_solve_ir(mspv_matrix_t A64, mspv_matrix_t Alo, const double* b,
+                                      double* x, double tol, double inner_tol,
+                                      int32_t max_outer, int32_t maxit_inner, void* stream,
+                                      int32_t* outer_iters, int32_t* inner_iters,
+                                      double* relres);
+
+/* Fill *info with the handle's shape, format and row statistics. */
+MSPV_API mspv_status mspv_info(mspv_matrix_t A, mspv_matrix_info* info);
+
+/*
+ * Copy the handle's stored structure to HOST arrays (values widened exactly to FP64):
+ *   COO: idx0 = rows[nnz], idx1 = cols[nnz], vals[nnz]
+ *   CSR: idx0 = irp[nrows + 1], idx1 = cols[nnz], vals[nnz]
+ *   DIA: idx0 = doff[ndiags], idx1 unused (may be NULL), vals[ndiags * npad]
+ * Sizes come from mspv_info. Synchronous.
+ */
+MSPV_API mspv_status mspv_export(mspv_matrix_t A, int32_t* idx0, int32_t* idx1, double* vals,
+                                 void* stream);
+
+/* Free the handle and its device memory (after synchronising its device). NULL is a no-op. */
+MSPV_API void mspv_destroy(mspv_matrix_t A);
+
+/* The calling thread's last error message ("" if none). Valid until the next call. */
+MSPV_API const char* mspv_last_error(void);
+
+/* Name of a status code. */
+MSPV_API const char* mspv_status_string(mspv_status s);
+
+/*
+ * Lanes per row used by the CSR SpMV kernel for the given row-length statistics
+ * (host only, no device access): the smallest power of two in [2, 32] not below
+ * the mean row length; rows longer than 32 entries on average use 32 lanes
+ * (a warp per row). MSPV_CSR_VEC overrides it. Exposed for tests and tuning.
+ */
+MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max);
+
+/* Library version, as MAJOR * 10000 + MINOR * 100 + PATCH. */
+MSPV_API int32_t mspv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSPV_H */

@@ -1,0 +1,206 @@
+"""mspv: sparse matrix-vector multiply over COO / CSR / DIA and conjugate gradient on
+GB300 (sm_103a), after "Morpheus unleashed" (arXiv 2304.09511).
+
+A thin binding over libmspv.so (include/mspv.h): every step runs in the library's
+CUDA kernels; this module only marshals arguments. PyTorch provides device memory
+and the current CUDA stream.
+
+    import paper_2304_09511_gb300 as mspv
+    A = mspv.Matrix.from_coo(n, n, rows, cols, vals)        # canonical COO on the GPU
+    D = A.convert("dia")                                     # or "csr"; value_type="f32"/"bf16"
+    y = D.spmv(x)                                            # x: CUDA float64 tensor
+    res = D.cg(b, tol=1e-10, maxit=1000)                     # res.x, res.iters, res.relres
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import MspvError, FORMATS, VALUE_TYPES, load
+
+__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "stream_handle"]
+
+_FMT_NAMES = {v: k for k, v in FORMATS.items()}
+_VT_NAMES = {v: k for k, v in VALUE_TYPES.items()}
+
+
+def stream_handle(stream=None) -> int:
+    """cudaStream_t of a torch stream (default: torch's current stream), as an int."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor, contiguous."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    return int(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+def csr_vector_width(row_mean: float, row_std: float = 0.0, row_max: int = 0) -> int:
+    return int(load().mspv_csr_vector_width(row_mean, row_std, row_max))
+
+
+@dataclass
+class CgResult:
+    x: object
+    status: int
+    iters: int
+    relres: float
+    outer_iters: int = 0
+
+    @property
+    def converged(self) -> bool:
+        return self.status == _lib.OK
+
+
+class Matrix:
+    """A handle on a sparse matrix held by libmspv (device memory owned by the handle)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    # -- lifecycle ---------------------------------------------------------------
+    @classmethod
+    def from_coo(cls, nrows: int, ncols: int, rows, cols, vals, stream=None) -> "Matrix":
+        """Triplets as numpy arrays (host) or torch tensors (host or CUDA); int32 indices,
+        float64 values. The handle holds the canonical form (sorted, duplicates summed)."""
+        lib = load()
+        rows, cols, vals = _as_contig(rows, np.int32), _as_contig(cols, np.int32), _as_contig(vals, np.float64)
+        n = int(rows.shape[0])
+        if not (int(cols.shape[0]) == n == int(vals.shape[0])):
+            raise ValueError("rows, cols and vals must have the same length")
+        (pr, dr), (pc, dc), (pv, dv) = _ptr(rows), _ptr(cols), _ptr(vals)
+        if not (dr == dc == dv):
+            raise ValueError("triplet arrays must all be on the host or all on the device")
+        out = ctypes.c_void_p()
+        s = stream_handle(stream) if dr else 0
+        _lib.check(lib.mspv_create_coo(nrows, ncols, n, pr or None, pc or None, pv or None, dr, s,
+                                       ctypes.byref(out)))
+        return cls(out.value)
+
+    def convert(self, fmt: str, value_type: str = "f64", stream=None) -> "Matrix":
+        lib = load()
+        out = ctypes.c_void_p()
+        _lib.check(lib.mspv_convert(self._h, FORMATS[fmt], VALUE_TYPES[value_type],
+                                    _stream_or_null(stream), ctypes.byref(out)))
+        return Matrix(out.value)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().mspv_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- description ---------------------------------------------------------------
+    @property
+    def info(self) -> dict:
+        inf = _lib.MatrixInfo()
+        _lib.check(load().mspv_info(self._h, ctypes.byref(inf)))
+        d = {name: getattr(inf, name) for name, _ in _lib.MatrixInfo._fields_}
+        d["format"] = _FMT_NAMES[d["format"]]
+        d["value_type"] = _VT_NAMES[d["value_type"]]
+        return d
+
+    @property
+    def shape(self):
+        i = self.info
+        return i["nrows"], i["ncols"]
+
+    def export(self) -> dict:
+        """Stored structure copied to host numpy arrays (values widened to float64)."""
+        inf = self.info
+        fmt, nnz, nr = inf["format"], inf["nnz"], inf["nrows"]
+        if fmt == "coo":
+            a0, a1, nv = np.empty(max(nnz, 1), np.int32), np.empty(max(nnz, 1), np.int32), nnz
+        elif fmt == "csr":
+            a0, a1, nv = np.empty(nr + 1, np.int32), np.empty(max(nnz, 1), np.int32), nnz
+        else:
+            a0, a1, nv = np.empty(max(inf["ndiags"], 1), np.int32), None, inf["ndiags"] * inf["npad"]
+        v = np.empty(max(nv, 1), np.float64)
+        _lib.check(load().mspv_export(self._h, a0.ctypes.data, None if a1 is None else a1.ctypes.data,
+                                      v.ctypes.data, _stream_or_null(None)))
+        if fmt == "coo":
+            return {"rows": a0[:nnz], "cols": a1[:nnz], "vals": v[:nv]}
+        if fmt == "csr":
+            return {"irp": a0, "cols": a1[:nnz], "vals": v[:nv]}
+        return {"doff": a0[:inf["ndiags"]], "vals": v[:nv], "npad": inf["npad"]}
+
+    # -- compute ---------------------------------------------------------------------
+    def spmv(self, x, y=None, stream=None):
+        """y = A x on the device (float64 CUDA tensors). Asynchronous on the stream."""
+        import torch
+        nr, nc = self.shape
+        _check_vec(x, nc)
+        if y is None:
+            y = torch.empty(nr, dtype=torch.float64, device=x.device)
+        _check_vec(y, nr)
+        _lib.check(load().mspv_spmv(self._h, x.data_ptr(), y.data_ptr(), stream_handle(stream)))
+        return y
+
+    def cg(self, b, x=None, tol: float = 1e-10, maxit: int = 1000, stream=None) -> CgResult:
+        """Unpreconditioned CG from x (zeros if None); x is overwritten in place."""
+        import torch
+        n = self.shape[0]
+        _check_vec(b, n)
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=b.device)
+        _check_vec(x, n)
+        it = ctypes.c_int32(0)
+        rr = ctypes.c_double(0.0)
+        st = load().mspv_cg_solve(self._h, b.data_ptr(), x.data_ptr(), float(tol), int(maxit),
+                                  stream_handle(stream), ctypes.byref(it), ctypes.byref(rr))
+        _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
+        return CgResult(x, st, it.value, rr.value)
+
+    def cg_ir(self, low: "Matrix", b, x=None, tol: float = 1e-10, inner_tol: float = 1e-6,
+              max_outer: int = 50, maxit_inner: int = 10000, stream=None) -> CgResult:
+        """Iterative refinement: FP64 residuals on self, inner CG on `low` (e.g. BF16 values)."""
+        import torch
+        n = self.shape[0]
+        _check_vec(b, n)
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=b.device)
+        _check_vec(x, n)
+        oi, ii, rr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+        st = load().mspv_cg_solve_ir(self._h, low._h, b.data_ptr(), x.data_ptr(), float(tol),
+                                     float(inner_tol), int(max_outer), int(maxit_inner),
+                                     stream_handle(stream), ctypes.byref(oi), ctypes.byref(ii),
+                                     ctypes.byref(rr))
+        _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
+        return CgResult(x, st, ii.value, rr.value, outer_iters=oi.value)
+
+
+def _as_contig(a, dtype):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=dtype)
+    import torch
+    tdt = {np.int32: torch.int32, np.float64: torch.float64}[dtype]
+    return a.to(tdt).contiguous()
+
+
+def _check_vec(v, n):
+    import torch
+    if not isinstance(v, torch.Tensor) or not v.is_cuda or v.dtype != torch.float64:
+        raise TypeError("vectors must be CUDA float64 tensors")
+    if v.numel() != n or not v.is_contiguous():
+        raise ValueError(f"vector must be contiguous with {n} entries (got {v.numel()})")
+
+
+def _stream_or_null(stream):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return stream_handle(stream)
+    except Exception:
+        pass
+    return None

@@ -1,0 +1,339 @@
+// Unpreconditioned conjugate gradient, the solver the paper's HPCG experiments run
+// with the preconditioner disabled (Sec. VI), and an FP64 iterative-refinement loop
+// around it for low-precision matrix values (not in the paper).
+//
+// One iteration is three kernels on the caller's stream, none of which waits on
+// the host:
+//   1. q = A p with p.q fused into the SpMV epilogue; the last CTA forms alpha.
+//   2. x += alpha p, r -= alpha q, with r.r fused; the last CTA forms rho', tests
+//      convergence, forms beta and counts the iteration.
+//   3. p = r + beta p.
+// Every scalar lives in a device CgState. Once `done` is set all kernels return
+// at entry, so the host may launch past convergence and polls the state only every
+// MSPV_CG_CHECK_EVERY iterations.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+
+#include "internal.cuh"
+
+namespace mspv {
+
+static int64_t vec_grid(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)kNumSMs * 8;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : b;
+}
+
+// Two fused sums reduced by the last CTA (partials holds 2 per CTA).
+__device__ __forceinline__ bool last_block_total2(double a, double b, double* partials,
+                                                  uint32_t* ticket, double* ta, double* tb) {
+    __shared__ double s_red[32];
+    __shared__ bool s_last;
+    const double sa = block_sum(a, s_red);
+    const double sb = block_sum(b, s_red);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = sa;
+        partials[2 * blockIdx.x + 1] = sb;
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc_a = 0.0, acc_b = 0.0;
+    for (uint32_t k = threadIdx.x; k < gridDim.x; k += kThreads) {
+        acc_a += __ldcg(partials + 2 * k);
+        acc_b += __ldcg(partials + 2 * k + 1);
+    }
+    const double totb = block_sum(acc_b, s_red);
+    const double tota = block_sum(acc_a, s_red);
+    if (threadIdx.x == 0) {
+        *ta = tota;
+        *tb = totb;
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// r = b - q (q = A x0), p = r; rho = r.r and ||b|| reduced; convergence at start.
+__global__ void __launch_bounds__(kThreads) cg_init_kernel(int64_t n, const double* __restrict__ b,
+                                                           const double* __restrict__ q,
+                                                           double* __restrict__ r, double* __restrict__ p,
+                                                           double* __restrict__ partials, CgState* st) {
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
+        const double bi = b[i];
+        const double ri = bi - q[i];
+        r[i] = ri;
+        p[i] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    double trr, tbb;
+    if (last_block_total2(rr, bb, partials, &st->ticket, &trr, &tbb) && threadIdx.x == 0) {
+        st->rho = trr;
+        st->bnorm = sqrt(tbb);
+        st->iters = 0;
+        if (tbb == 0.0 || sqrt(trr) <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; rho' = r.r; convergence, beta, iteration count.
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* __restrict__ x,
+                                                             double* __restrict__ r,
+                                                             const double* __restrict__ p,
+                                                             const double* __restrict__ q,
+                                                             double* __restrict__ partials, CgState* st) {
+    if (st->done) return;
+    const double alpha = st->alpha;
+    double rr = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {
+        const int64_t i2 = i + stride;
+        const double x0 = x[i], x1 = x[i2], p0 = p[i], p1 = p[i2];
+        const double r0 = r[i], r1 = r[i2], q0 = q[i], q1 = q[i2];
+        x[i] = fma(alpha, p0, x0);
+        x[i2] = fma(alpha, p1, x1);
+        const double n0 = fma(-alpha, q0, r0), n1 = fma(-alpha, q1, r1);
+        r[i] = n0;
+        r[i2] = n1;
+        rr = fma(n0, n0, rr);
+        rr = fma(n1, n1, rr);
+    }
+    if (i < n) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double n0 = fma(-alpha, q[i], r[i]);
+        r[i] = n0;
+        rr = fma(n0, n0, rr);
+    }
+    double tot;
+    if (last_block_total(rr, partials, &st->ticket, &tot) && threadIdx.x == 0) {
+        st->iters += 1;
+        if (sqrt(tot) <= st->tol * st->bnorm) {
+            st->rho = tot;
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        } else {
+            st->beta = tot / st->rho;
+            st->rho = tot;
+            if (st->iters >= st->maxit) {
+                st->done = 1;
+                st->phase = CG_MAXIT;
+            }
+        }
+    }
+}
+
+// p = r + beta p
+__global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
+                                                              double* __restrict__ p,
+                                                              const CgState* st) {
+    if (st->done) return;
+    const double beta = st->beta;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {
+        const int64_t i2 = i + stride;
+        const double r0 = r[i], r1 = r[i2], p0 = p[i], p1 = p[i2];
+        p[i] = fma(beta, p0, r0);
+        p[i2] = fma(beta, p1, r1);
+    }
+    if (i < n) p[i] = fma(beta, p[i], r[i]);
+}
+
+// Iterative refinement helpers: r = b - q with rho = r.r (and ||b|| on the first call).
+__global__ void __launch_bounds__(kThreads) ir_residual_kernel(int64_t n, const double* __restrict__ b,
+                                                               const double* __restrict__ q,
+                                                               double* __restrict__ r,
+                                                               double* __restrict__ partials, CgState* st) {
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
+        const double bi = b[i];
+        const double ri = bi - q[i];
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    double trr, tbb;
+    if (last_block_total2(rr, bb, partials, &st->ticket, &trr, &tbb) && threadIdx.x == 0) {
+        st->rho = trr;
+        st->bnorm = sqrt(tbb);
+    }
+}
+
+__global__ void axpy1_kernel(int64_t n, double* __restrict__ x, const double* __restrict__ d) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+
+__global__ void zero_kernel(double* __restrict__ v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static mspv_status ensure_cg_work(mspv_matrix* A) {
+    CgWork& w = A->cg;
+    const int64_t n = A->nrows;
+    const int64_t need_partials = 2 * std::max<int64_t>(spmv_partials_needed(A), vec_grid(n));
+    if (w.r && w.n == n && w.npartials >= need_partials) return MSPV_OK;
+    auto f = [](void* p) { if (p) dev_free(p, 0); };
+    f(w.r); f(w.p); f(w.q); f(w.partials); f(w.st);
+    w.r = w.p = w.q = w.partials = nullptr;
+    w.st = nullptr;
+    MSPV_TRY(dev_alloc_n(&w.r, n));
+    MSPV_TRY(dev_alloc_n(&w.p, n));
+    MSPV_TRY(dev_alloc_n(&w.q, n));
+    MSPV_TRY(dev_alloc_n(&w.partials, need_partials));
+    MSPV_TRY(dev_alloc_n(&w.st, 2));   // [0] CG, [1] iterative-refinement outer loop
+    if (!w.host_st) MSPV_CUDA_TRY(cudaMallocHost((void**)&w.host_st, 2 * sizeof(CgState)));
+    w.n = n;
+    w.npartials = need_partials;
+    return MSPV_OK;
+}
+
+static int check_every() {
+    const char* s = std::getenv("MSPV_CG_CHECK_EVERY");
+    const int v = s ? std::atoi(s) : 10;
+    return v > 0 ? v : 10;
+}
+
+mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,
+                     cudaStream_t s, int32_t* iters, double* relres) {
+    if (A->nrows != A->ncols)
+        return set_error(MSPV_EFORMAT, "cg: matrix is %d x %d, not square", A->nrows, A->ncols);
+    if (maxit < 0) return set_error(MSPV_EINVAL, "cg: maxit < 0");
+    const int64_t n = A->nrows;
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    if (n == 0) return MSPV_OK;
+    if (A->format == MSPV_COO && A->nnz == 0) return set_error(MSPV_EINVAL, "cg: matrix has no entries");
+    MSPV_TRY(ensure_cg_work(A));
+    CgWork& w = A->cg;
+    CgState* hst = w.host_st;
+    *hst = CgState{};
+    hst->tol = tol;
+    hst->maxit = maxit;
+    MSPV_CUDA_TRY(cudaMemcpyAsync(w.st, hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    const unsigned G = (unsigned)vec_grid(n);
+
+    MSPV_TRY(launch_spmv(A, x, w.q, s, DotEpilogue{nullptr, nullptr}));
+    cg_init_kernel<<<G, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.st);
+    MSPV_CUDA_TRY(cudaGetLastError());
+    MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hst->bnorm == 0.0) {   // b = 0: the solution is 0
+        zero_kernel<<<G, kThreads, 0, s>>>(x, n);
+        MSPV_CUDA_TRY(cudaGetLastError());
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        return MSPV_OK;
+    }
+    const DotEpilogue ep{w.st, w.partials};
+    const int every = check_every();
+    int32_t launched = 0;
+    while (!hst->done && launched < maxit) {
+        const int32_t batch = std::min<int32_t>(every, maxit - launched);
+        for (int32_t k = 0; k < batch; ++k) {
+            MSPV_TRY(launch_spmv(A, w.p, w.q, s, ep));
+            cg_update_kernel<<<G, kThreads, 0, s>>>(n, x, w.r, w.p, w.q, w.partials, w.st);
+            cg_pupdate_kernel<<<G, kThreads, 0, s>>>(n, w.r, w.p, w.st);
+        }
+        MSPV_CUDA_TRY(cudaGetLastError());
+        launched += batch;
+        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (iters) *iters = hst->iters;
+    if (relres) *relres = std::sqrt(hst->rho) / hst->bnorm;
+    switch (hst->phase) {
+        case CG_CONVERGED:
+            return MSPV_OK;
+        case CG_BREAKDOWN:
+            return set_error(MSPV_EBREAKDOWN, "cg: breakdown at iteration %d (p.Ap = %g)", hst->iters, hst->pq);
+        default:   // reached maxit (or maxit == 0)
+            if (tol <= 0.0) return MSPV_OK;
+            return set_error(MSPV_ENOTCONV, "cg: %d iterations, relative residual %g above %g", hst->iters,
+                             std::sqrt(hst->rho) / hst->bnorm, tol);
+    }
+}
+
+mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, double* x,
+                        double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
+                        cudaStream_t s, int32_t* outer_iters, int32_t* inner_iters,
+                        double* relres) {
+    if (A64->nrows != A64->ncols || Alo->nrows != A64->nrows || Alo->ncols != A64->ncols)
+        return set_error(MSPV_EFORMAT, "cg_ir: matrices must be square and of equal size");
+    if (max_outer < 0 || maxit_inner < 0) return set_error(MSPV_EINVAL, "cg_ir: negative iteration limit");
+    const int64_t n = A64->nrows;
+    if (outer_iters) *outer_iters = 0;
+    if (inner_iters) *inner_iters = 0;
+    if (relres) *relres = 0.0;
+    if (n == 0) return MSPV_OK;
+    MSPV_TRY(ensure_cg_work(A64));
+    // outer vectors are separate buffers so that Alo may be the same handle as A64
+    DevBuf rbuf, dbuf, qbuf;
+    MSPV_TRY(rbuf.alloc(sizeof(double) * n));
+    MSPV_TRY(dbuf.alloc(sizeof(double) * n));
+    MSPV_TRY(qbuf.alloc(sizeof(double) * n));
+    double* r = rbuf.as<double>();
+    double* d = dbuf.as<double>();
+    double* q = qbuf.as<double>();
+    CgState* ost = A64->cg.st + 1;
+    CgState* host = A64->cg.host_st + 1;
+    *host = CgState{};
+    MSPV_CUDA_TRY(cudaMemcpyAsync(ost, host, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    const unsigned G = (unsigned)vec_grid(n);
+    int32_t total_inner = 0;
+    mspv_status result = MSPV_ENOTCONV;
+    for (int32_t k = 0;; ++k) {
+        MSPV_TRY(launch_spmv(A64, x, q, s, DotEpilogue{nullptr, nullptr}));
+        ir_residual_kernel<<<G, kThreads, 0, s>>>(n, b, q, r, A64->cg.partials, ost);
+        MSPV_CUDA_TRY(cudaGetLastError());
+        MSPV_CUDA_TRY(cudaMemcpyAsync(host, ost, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (host->bnorm == 0.0) {
+            zero_kernel<<<G, kThreads, 0, s>>>(x, n);
+            MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+            result = MSPV_OK;
+            break;
+        }
+        const double rel = std::sqrt(host->rho) / host->bnorm;
+        if (relres) *relres = rel;
+        if (outer_iters) *outer_iters = k;
+        if (rel <= tol) { result = MSPV_OK; break; }
+        if (k == max_outer) { result = MSPV_ENOTCONV; break; }
+        zero_kernel<<<G, kThreads, 0, s>>>(d, n);
+        int32_t it = 0;
+        double inner_rel = 0.0;
+        const mspv_status st = cg_solve(Alo, r, d, inner_tol, maxit_inner, s, &it, &inner_rel);
+        total_inner += it;
+        if (st == MSPV_EBREAKDOWN || st == MSPV_ECUDA || st == MSPV_ENOMEM || st == MSPV_EINVAL) {
+            result = st;
+            break;
+        }
+        axpy1_kernel<<<G, kThreads, 0, s>>>(n, x, d);
+        MSPV_CUDA_TRY(cudaGetLastError());
+    }
+    if (inner_iters) *inner_iters = total_inner;
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (result == MSPV_ENOTCONV)
+        return set_error(MSPV_ENOTCONV, "cg_ir: %d corrections, residual above %g", max_outer, tol);
+    if (result != MSPV_OK) return result;
+    clear_error();
+    return MSPV_OK;
+}
+
+}  // namespace mspv

@@ -1,0 +1,250 @@
+// Internal declarations shared by the translation units of libmspv.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "mspv.h"
+
+namespace mspv {
+
+constexpr int kThreads = 256;       // threads per CTA for every kernel here
+constexpr int kNumSMs = 152;        // GB300: 2 dies x 76 SMs
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+mspv_status set_error(mspv_status s, const char* fmt, ...);
+void clear_error();
+
+#define MSPV_CUDA_TRY(expr)                                                              \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return ::mspv::set_error(MSPV_ECUDA, "%s failed: %s (%s:%d)", #expr,         \
+                                     cudaGetErrorString(_e), __FILE__, __LINE__);        \
+    } while (0)
+
+#define MSPV_TRY(expr)                              \
+    do {                                            \
+        mspv_status _s = (expr);                    \
+        if (_s != MSPV_OK) return _s;               \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory: every allocation goes through here so that MSPV_MAX_BYTES can cap
+// the total the library holds (ENOMEM is then returned without exhausting the GPU).
+// ---------------------------------------------------------------------------
+mspv_status dev_alloc(void** p, size_t bytes);
+void dev_free(void* p, size_t bytes);
+
+template <typename T>
+mspv_status dev_alloc_n(T** p, int64_t count) {
+    return dev_alloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+// A device buffer freed on scope exit (synchronous free; used by converters).
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { reset(); }
+    void reset() {
+        if (ptr) dev_free(ptr, bytes);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    mspv_status alloc(size_t b) {
+        reset();
+        bytes = b > 0 ? b : 1;
+        mspv_status s = dev_alloc(&ptr, bytes);
+        if (s != MSPV_OK) bytes = 0;
+        return s;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(ptr); }
+};
+
+// ---------------------------------------------------------------------------
+// value storage types
+// ---------------------------------------------------------------------------
+inline size_t value_size(int vt) { return vt == MSPV_F64 ? 8 : (vt == MSPV_F32 ? 4 : 2); }
+
+// ---------------------------------------------------------------------------
+// CG device state: scalars live on the device so the loop needs no host sync.
+// ---------------------------------------------------------------------------
+enum CgPhase : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
+
+struct CgState {
+    double rho;      // r.r of the current residual
+    double pq;       // p.q of the current step
+    double alpha;
+    double beta;
+    double bnorm;    // ||b||_2
+    double tol;
+    int32_t iters;
+    int32_t maxit;
+    int32_t done;    // nonzero once converged, at maxit, or broken down
+    int32_t phase;   // CgPhase
+    uint32_t ticket; // last-block counter of the fused reductions (reset by the last block)
+    uint32_t pad;
+};
+
+// Where an SpMV kernel's optional fused epilogue writes: the dot x.y of its input
+// and output (CG's p.q), reduced across CTAs by the last CTA to finish, which then
+// forms alpha = rho / p.q. st == nullptr disables the epilogue.
+struct DotEpilogue {
+    CgState* st;
+    double* partials;   // one per CTA of the launch
+};
+
+// COO per-chunk carry record for the segmented SpMV.
+struct CooCarry {
+    int32_t row_first;
+    int32_t row_last;
+    double head;   // partial sum of row_first over the chunk
+    double tail;   // partial sum of row_last over the chunk
+};
+
+constexpr int kCooWarpIters = 8;                 // 32 x 8 = 256 entries per warp chunk
+constexpr int kCooChunk = 32 * kCooWarpIters;
+
+// CG workspace, owned by a handle and grown on demand.
+struct CgWork {
+    int64_t n = 0;
+    double* r = nullptr;
+    double* p = nullptr;
+    double* q = nullptr;
+    double* partials = nullptr;
+    int64_t npartials = 0;
+    CgState* st = nullptr;
+    CgState* host_st = nullptr;   // pinned mirror
+};
+
+// Last CTA of a fused p.q reduction: alpha = rho / p.q, or a breakdown when p.q <= 0
+// or alpha is not finite (the matrix is not SPD, or the iteration has degenerated).
+__device__ __forceinline__ void finish_alpha(CgState* st, double pq) {
+    st->pq = pq;
+    const double alpha = st->rho / pq;
+    if (!(pq > 0.0) || !isfinite(alpha)) {
+        st->phase = CG_BREAKDOWN;
+        st->done = 1;
+    } else {
+        st->alpha = alpha;
+    }
+}
+
+}  // namespace mspv
+
+// The handle. Device arrays are owned; sizes in elements.
+struct mspv_matrix {
+    int32_t format = MSPV_COO;
+    int32_t value_type = MSPV_F64;
+    int32_t nrows = 0, ncols = 0;
+    int64_t nnz = 0;
+    int32_t ndiags = 0, npad = 0;
+    int32_t csr_vector = 0;
+    int32_t row_max = 0;
+    double row_mean = 0.0, row_std = 0.0;
+    int64_t empty_rows = 0;
+    int device = 0;
+
+    int32_t* ai = nullptr;    // COO rows
+    int32_t* aj = nullptr;    // COO / CSR columns
+    int32_t* irp = nullptr;   // CSR row pointers
+    int32_t* doff = nullptr;  // DIA offsets
+    void* av = nullptr;       // values (value_type)
+    int64_t av_count = 0;
+
+    mspv::CooCarry* carry = nullptr;   // COO: per-chunk carries
+    int64_t nchunks = 0;
+
+    mspv::CgWork cg;
+    int64_t bytes = 0;        // device bytes held
+};
+
+namespace mspv {
+
+// scan.cu / convert.cu
+mspv_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t m, int32_t* d_total,
+                               cudaStream_t s);
+mspv_status build_coo(int32_t nrows, int32_t ncols, int64_t nnz, const int32_t* rows,
+                      const int32_t* cols, const double* vals, cudaStream_t s,
+                      mspv_matrix* M);
+mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStream_t s,
+                       mspv_matrix* M);
+mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, double* vals,
+                          cudaStream_t s);
+void free_matrix(mspv_matrix* M);
+mspv_status ensure_coo_carry(mspv_matrix* M);
+mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
+
+// spmv.cu
+mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
+                        DotEpilogue ep);
+int64_t spmv_partials_needed(const mspv_matrix* A);   // CTAs of the fused-dot launch
+int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
+
+// cg.cu
+mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,
+                     cudaStream_t s, int32_t* iters, double* relres);
+mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, double* x,
+                        double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
+                        cudaStream_t s, int32_t* outer_iters, int32_t* inner_iters,
+                        double* relres);
+
+// block-wide reductions shared by the kernels (defined inline below)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA (kThreads threads); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* smem32) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) smem32[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = (lane < (kThreads / 32)) ? smem32[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+// Fused cross-CTA reduction: every CTA posts its partial; the last CTA to arrive
+// (atomic ticket, no waiting) sums all partials in index order, so the result is
+// deterministic. Returns true in exactly one CTA, where thread 0 holds *total.
+__device__ __forceinline__ bool last_block_total(double partial, double* partials,
+                                                 uint32_t* ticket, double* total) {
+    __shared__ double s_red[32];
+    __shared__ bool s_last;
+    double bsum = block_sum(partial, s_red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = bsum;
+        __threadfence();
+        uint32_t t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (uint32_t b = threadIdx.x; b < gridDim.x; b += kThreads) acc += __ldcg(partials + b);
+    double tot = block_sum(acc, s_red);
+    if (threadIdx.x == 0) {
+        *total = tot;
+        *ticket = 0u;
+    }
+    return true;
+}
+
+}  // namespace mspv

@@ -121,3 +121,26 @@ def random_coo(nrows: int, ncols: int, nnz: int, seed: int, dup_frac: float = 0.
         p = rng.permutation(r.size)
         r, c, v = r[p], c[p], v[p]
     return r.astype(np.int32), c.astype(np.int32), v.astype(np.float64)
+
+
+def banded(n: int, k: int, seed: int, fill: float = 1.0, spread: int | None = None):
+    """Square matrix with k distinct diagonals (offsets drawn from [-spread, spread],
+    always including 0), each in-range slot kept with probability ``fill``; values
+    U(-1, 1). Triplets in random order."""
+    rng = np.random.default_rng(seed)
+    spread = max(1, n - 1) if spread is None else min(spread, max(n - 1, 0))
+    pool = np.arange(-spread, spread + 1)
+    pool = pool[pool != 0]
+    k = max(1, min(k, pool.size + 1))
+    offs = np.sort(np.concatenate([[0], rng.choice(pool, k - 1, replace=False)])) if n > 1 else np.array([0])
+    rows, cols = [], []
+    for off in offs.tolist():
+        i = np.arange(max(0, -off), min(n, n - off))
+        keep = rng.random(i.size) < fill
+        rows.append(i[keep])
+        cols.append(i[keep] + off)
+    r = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    c = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    v = rng.uniform(-1.0, 1.0, r.size)
+    p = rng.permutation(r.size)
+    return r[p].astype(np.int32), c[p].astype(np.int32), v[p]

@@ -1,0 +1,168 @@
+"""GPU parity for CG (and iterative refinement) through the C ABI against the CPU
+oracle: the 27-point stencil of the HPCG experiments, plus the special cases."""
+import numpy as np
+import pytest
+
+import synth
+from _parity import assert_spmv_parity, assert_structure_equal
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mspv():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_09511_gb300 as m
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def stencil16(mspv, orc):
+    g = 16
+    n = g ** 3
+    r, c, v = synth.stencil27(g)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    O = orc.canonicalize(n, n, r, c, v)
+    return g, n, A, O
+
+
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_stencil16_structure_spmv(mspv, orc, stencil16, fmt):
+    """The small HPCG case: 16^3 grid, n = 4096, nnz = 46^3 = 97,336, 27 diagonals."""
+    g, n, A, O = stencil16
+    assert O.nnz == (3 * g - 2) ** 3
+    M = A if fmt == "coo" else A.convert(fmt)
+    Of = orc.convert(O, fmt)
+    assert_structure_equal(M, Of, orc)
+    if fmt == "dia":
+        assert M.info["ndiags"] == 27
+    x = synth.uniform_x(n, 0)
+    assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), Of, x, orc)
+
+
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_stencil16_cg_matches_oracle(mspv, orc, stencil16, fmt):
+    g, n, A, O = stencil16
+    M = A if fmt == "coo" else A.convert(fmt)
+    Of = orc.convert(O, fmt)
+    b = orc.spmv(Of, np.ones(n))
+    res = M.cg(dev(b), tol=1e-10, maxit=1000)
+    xo, st, k, rel, _, _ = orc.cg(Of, b, tol=1e-10, maxit=1000)
+    assert res.converged and st == orc.OK
+    assert abs(res.iters - k) <= 1
+    assert res.relres <= 1e-10
+    x = res.x.cpu().numpy()
+    true = np.linalg.norm(b - orc.spmv(Of, x)) / np.linalg.norm(b)
+    assert true <= 1.5e-10
+    # both iterates approximate x = 1 to within kappa * 1e-10 (kappa ~ 39 at g = 16)
+    assert np.max(np.abs(x - xo)) <= 1e-8
+    assert np.max(np.abs(x - 1.0)) <= 40 * 1e-10 * np.sqrt(n)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "dia"])
+def test_fixed_iterations_track_oracle(mspv, orc, stencil16, fmt):
+    """tol = 0 runs exactly maxit iterations; iterates agree with the oracle's."""
+    g, n, A, O = stencil16
+    M = A.convert(fmt)
+    Of = orc.convert(O, fmt)
+    b = synth.uniform_x(n, 7)
+    for k in (1, 2, 5, 20):
+        res = M.cg(dev(b), tol=0.0, maxit=k)
+        xo, st, ko, rel, _, _ = orc.cg(Of, b, tol=0.0, maxit=k)
+        assert res.converged and res.iters == k == ko
+        assert np.max(np.abs(res.x.cpu().numpy() - xo)) <= 1e-12 * np.max(np.abs(xo)) * k
+        assert res.relres == pytest.approx(rel, rel=1e-9)
+
+
+def test_cg_nonzero_start_and_restart(mspv, orc, stencil16):
+    """x0 is honoured; resuming from a saved iterate is the same as one longer run
+    up to rounding (checkpoint/resume is calling again with the saved x)."""
+    g, n, A, O = stencil16
+    D = A.convert("dia")
+    b = orc.spmv(orc.convert(O, "dia"), np.ones(n))
+    x0 = synth.uniform_x(n, 3)
+    res = D.cg(dev(b), x=dev(x0.copy()), tol=1e-10, maxit=1000)
+    xo, st, k, rel, _, _ = orc.cg(orc.convert(O, "dia"), b, x0=x0, tol=1e-10, maxit=1000)
+    assert res.converged and abs(res.iters - k) <= 1
+    part = D.cg(dev(b), tol=0.0, maxit=10)
+    resumed = D.cg(dev(b), x=part.x, tol=1e-10, maxit=1000)
+    assert resumed.converged
+    assert np.max(np.abs(resumed.x.cpu().numpy() - 1.0)) <= 1e-7
+
+
+def test_cg_special_cases(mspv):
+    n = 1000
+    d = np.arange(1.0, n + 1)
+    idx = np.arange(n, dtype=np.int32)
+    A = mspv.Matrix.from_coo(n, n, idx, idx, d).convert("csr")
+    # b = 0 -> x = 0, zero iterations
+    res = A.cg(torch.zeros(n, dtype=torch.float64, device="cuda"),
+               x=torch.ones(n, dtype=torch.float64, device="cuda"), tol=1e-10, maxit=10)
+    assert res.converged and res.iters == 0 and torch.all(res.x == 0)
+    # iteration limit -> ENOTCONV with the last iterate
+    b = torch.ones(n, dtype=torch.float64, device="cuda")
+    res = A.cg(b, tol=1e-14, maxit=3)
+    assert res.status == 6 and res.iters == 3
+    # indefinite -> EBREAKDOWN before any update
+    ind = mspv.Matrix.from_coo(2, 2, np.array([0, 1], np.int32), np.array([0, 1], np.int32),
+                               np.array([1.0, -1.0])).convert("dia")
+    res = ind.cg(torch.ones(2, dtype=torch.float64, device="cuda"), tol=1e-10, maxit=10)
+    assert res.status == 7 and res.iters == 0
+    assert torch.all(res.x == 0)
+    # diagonal with m distinct eigenvalues: at most m iterations
+    m = 5
+    dd = np.linspace(1.0, 10.0, m)[np.arange(n) % m]
+    Dm = mspv.Matrix.from_coo(n, n, idx, idx, dd).convert("dia")
+    res = Dm.cg(b, tol=1e-12, maxit=50)
+    assert res.converged and res.iters <= m
+    # rectangular -> EFORMAT
+    R = mspv.Matrix.from_coo(3, 4, np.array([0], np.int32), np.array([3], np.int32), np.array([1.0]))
+    with pytest.raises(mspv.MspvError, match="EFORMAT"):
+        R.cg(torch.ones(3, dtype=torch.float64, device="cuda"), x=torch.zeros(3, dtype=torch.float64, device="cuda"))
+
+
+def test_check_interval_does_not_change_result(mspv, stencil16, monkeypatch):
+    g, n, A, O = stencil16
+    D = A.convert("dia")
+    b = dev(synth.uniform_x(n, 1))
+    outs = []
+    for every in ("1", "7", "1000"):
+        monkeypatch.setenv("MSPV_CG_CHECK_EVERY", every)
+        res = D.cg(b, tol=1e-10, maxit=500)
+        outs.append((res.iters, res.x.cpu().numpy().copy()))
+    assert outs[0][0] == outs[1][0] == outs[2][0]
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][1], outs[2][1])
+
+
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("fmt", ["csr", "dia"])
+def test_iterative_refinement(mspv, orc, vt, fmt):
+    """Perturbed SPD stencil whose values are not exact in FP32/BF16: the FP64 outer loop
+    still reaches 1e-10 relative residual; the answer matches the oracle's IR."""
+    g = 20
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 3)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    A64 = A.convert(fmt)
+    Alo = A.convert(fmt, vt)
+    O = orc.convert(orc.canonicalize(n, n, r, c, v), fmt)
+    Olo = orc.with_values(O, vt)
+    assert not np.array_equal(Olo.av, O.av)
+    b = orc.spmv(O, np.ones(n))
+    res = A64.cg_ir(Alo, dev(b), tol=1e-10, inner_tol=1e-4)
+    xo, st, outer, inner, rel = orc.cg_ir(O, Olo, b, tol=1e-10, inner_tol=1e-4)
+    assert res.converged and st == orc.OK
+    assert res.relres <= 1e-10
+    x = res.x.cpu().numpy()
+    assert np.linalg.norm(b - orc.spmv(O, x)) / np.linalg.norm(b) <= 1.5e-10
+    assert abs(res.outer_iters - outer) <= 1
+    assert np.max(np.abs(x - xo)) <= 1e-8

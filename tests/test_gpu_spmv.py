@@ -1,0 +1,231 @@
+"""GPU parity: format converters (bit-exact) and SpMV (per-row FP64 bound) through the
+C ABI, against the CPU oracle on the same seeded inputs."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from _parity import assert_spmv_parity, assert_structure_equal
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mspv():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_09511_gb300 as m
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+CASES = [
+    # (nrows, ncols, nnz, seed, dup_frac, empty_rows)
+    (1, 1, 1, 0, 0.0, 0),
+    (1, 1, 5, 1, 0.8, 0),
+    (5, 5, 11, 2, 0.0, 0),
+    (7, 13, 30, 3, 0.2, 2),
+    (13, 7, 30, 4, 0.2, 3),
+    (64, 64, 700, 6, 0.3, 9),
+    (64, 64, 4096, 7, 0.0, 0),
+    (300, 300, 257, 8, 0.0, 100),        # just over one COO chunk, many empty rows
+    (1000, 1000, 4097, 9, 0.1, 50),      # one radix tile + 1, ragged
+    (20000, 20000, 333_333, 10, 0.05, 2000),   # many tiles, ragged tails
+    (5000, 37000, 100_001, 11, 0.0, 7),  # rectangular, wide
+    (37000, 5000, 100_001, 12, 0.02, 7),  # rectangular, tall
+]
+
+
+def build_pair(mspv, orc, case, on_device):
+    nrows, ncols, nnz, seed, dup, empty = case
+    r, c, v = synth.random_coo(nrows, ncols, nnz, seed, dup_frac=dup, empty_rows=empty)
+    if on_device:
+        A = mspv.Matrix.from_coo(nrows, ncols, dev(r), dev(c), dev(v))
+    else:
+        A = mspv.Matrix.from_coo(nrows, ncols, r, c, v)
+    O = orc.canonicalize(nrows, ncols, r, c, v)
+    return A, O
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}nnz{c[2]}")
+@pytest.mark.parametrize("on_device", [False, True], ids=["host_in", "dev_in"])
+def test_canonical_coo_bit_exact(mspv, orc, case, on_device):
+    A, O = build_pair(mspv, orc, case, on_device)
+    assert A.info["nnz"] == O.nnz
+    assert_structure_equal(A, O, orc)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}nnz{c[2]}")
+def test_csr_and_dia_bit_exact(mspv, orc, case):
+    A, O = build_pair(mspv, orc, case, True)
+    C = A.convert("csr")
+    assert_structure_equal(C, orc.coo_to_csr(O), orc)
+    inf = C.info
+    lens = np.bincount(O.ai, minlength=case[0])[:case[0]]
+    assert inf["row_max"] == (lens.max() if lens.size else 0)
+    assert inf["empty_rows"] == int(np.sum(lens == 0))
+    assert inf["row_mean"] == pytest.approx(O.nnz / case[0])
+    if case[0] == case[1]:
+        G = orc.coo_to_dia(O)
+        if G.ndiags * G.npad > max(32 * O.nnz, 1 << 20):
+            with pytest.raises(mspv.MspvError, match="ETOOBIG"):
+                A.convert("dia")
+        else:
+            assert_structure_equal(A.convert("dia"), G, orc)
+            # CSR-sourced DIA is the same structure
+            assert_structure_equal(C.convert("dia"), G, orc)
+    else:
+        with pytest.raises(mspv.MspvError, match="EFORMAT"):
+            A.convert("dia")
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}nnz{c[2]}")
+@pytest.mark.parametrize("fmt", ["coo", "csr"])
+def test_spmv_parity(mspv, orc, case, fmt):
+    A, O = build_pair(mspv, orc, case, True)
+    M = A if fmt == "coo" else A.convert(fmt)
+    Of = orc.convert(O, fmt)
+    x = synth.uniform_x(case[1], case[3]) * 2 - 1
+    y = M.spmv(dev(x)).cpu().numpy()
+    assert_spmv_parity(y, Of, x, orc)
+
+
+BANDED = [
+    # (n, k diagonals, seed, fill, spread)
+    (1, 1, 0, 1.0, None),
+    (5, 3, 1, 1.0, None),
+    (33, 9, 2, 0.7, None),
+    (64, 127, 3, 1.0, None),        # dense: every diagonal
+    (1000, 27, 4, 0.9, 60),
+    (20001, 27, 5, 1.0, 300),       # ragged against the 32-row padding and the tiles
+    (50000, 40, 6, 0.5, 49000),     # far offsets: long out-of-range stretches
+]
+
+
+@pytest.mark.parametrize("case", BANDED, ids=lambda c: f"n{c[0]}k{c[1]}")
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_banded_structure_and_spmv(mspv, orc, case, fmt):
+    n, k, seed, fill, spread = case
+    r, c, v = synth.banded(n, k, seed, fill, spread)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    O = orc.convert(orc.canonicalize(n, n, r, c, v), fmt)
+    M = A if fmt == "coo" else A.convert(fmt)
+    assert_structure_equal(M, O, orc)
+    x = synth.uniform_x(n, seed) * 2 - 1
+    assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), O, x, orc)
+
+
+@pytest.mark.parametrize("vec", [1, 2, 4, 8, 16, 32])
+def test_csr_every_vector_width(mspv, orc, vec, monkeypatch):
+    monkeypatch.setenv("MSPV_CSR_VEC", str(vec))
+    case = (3000, 3000, 60_000, 21, 0.0, 30)
+    A, O = build_pair(mspv, orc, case, True)
+    C = A.convert("csr")
+    assert C.info["csr_vector"] == vec
+    x = synth.uniform_x(case[1], 5)
+    assert_spmv_parity(C.spmv(dev(x)).cpu().numpy(), orc.coo_to_csr(O), x, orc)
+
+
+def test_long_rows_and_chunk_spanning(mspv, orc):
+    """A 20,000-entry row spans ~80 COO chunks; short rows around it; empty rows at both ends."""
+    rng = np.random.default_rng(3)
+    n = 30000
+    r = np.concatenate([np.full(20000, 17000), rng.integers(100, 29000, 50000), [5, 5, 29990]])
+    c = np.concatenate([rng.permutation(n)[:20000], rng.integers(0, n, 50003)])
+    v = rng.uniform(-1, 1, r.size)
+    A = mspv.Matrix.from_coo(n, n, dev(r.astype(np.int32)), dev(c.astype(np.int32)), dev(v))
+    O = orc.canonicalize(n, n, r, c, v)
+    x = synth.uniform_x(n, 9)
+    for fmt in ("coo", "csr"):
+        M = A if fmt == "coo" else A.convert(fmt)
+        assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), orc.convert(O, fmt), x, orc)
+
+
+def test_all_entries_in_one_row(mspv, orc):
+    n = 4000
+    rng = np.random.default_rng(4)
+    r = np.full(3000, 1234, np.int32)
+    c = rng.integers(0, n, 3000).astype(np.int32)
+    v = rng.uniform(-1, 1, 3000)
+    A = mspv.Matrix.from_coo(n, n, r, c, v)
+    O = orc.canonicalize(n, n, r, c, v)
+    x = synth.uniform_x(n, 1)
+    for fmt in ("coo", "csr"):
+        M = A if fmt == "coo" else A.convert(fmt)
+        y = M.spmv(dev(x)).cpu().numpy()
+        assert_spmv_parity(y, orc.convert(O, fmt), x, orc)
+        assert np.count_nonzero(y) == 1
+
+
+def test_empty_matrix_gives_zero(mspv):
+    A = mspv.Matrix.from_coo(10, 7, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    for M in (A, A.convert("csr")):
+        y = torch.full((10,), 5.0, dtype=torch.float64, device="cuda")
+        M.spmv(torch.ones(7, dtype=torch.float64, device="cuda"), y)
+        assert torch.all(y == 0)
+
+
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_low_precision_values(mspv, orc, vt, fmt):
+    n = 20001
+    r, c, v = synth.banded(n, 27, 7, 0.95, 500)
+    v = v * 37.0   # values over several binades so rounding is exercised
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    O = orc.canonicalize(n, n, r, c, v)
+    M = A.convert(fmt, vt)
+    assert M.info["value_type"] == vt
+    Of = orc.with_values(orc.convert(O, fmt), vt)
+    assert_structure_equal(M, Of, orc)   # rounding is bit-exact with the oracle's
+    x = synth.uniform_x(n, 2)
+    assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), Of, x, orc)
+
+
+def test_spmv_is_deterministic(mspv):
+    r, c, v = synth.random_coo(50000, 50000, 800_000, 41, dup_frac=0.05)
+    A = mspv.Matrix.from_coo(50000, 50000, dev(r), dev(c), dev(v))
+    x = dev(synth.uniform_x(50000, 3))
+    for M in (A, A.convert("csr")):
+        y1 = M.spmv(x).clone()
+        y2 = M.spmv(x)
+        assert torch.equal(y1, y2)
+
+
+def test_device_triplets_out_of_range_rejected(mspv):
+    r = dev(np.array([0, 1, 7], np.int32))
+    c = dev(np.array([0, 1, 1], np.int32))
+    v = dev(np.array([1.0, 2.0, 3.0]))
+    with pytest.raises(mspv.MspvError, match="EINVAL"):
+        mspv.Matrix.from_coo(3, 3, r, c, v)
+    # the context stays usable
+    A = mspv.Matrix.from_coo(3, 3, dev(np.array([0, 2], np.int32)), dev(np.array([1, 2], np.int32)),
+                             dev(np.array([1.0, 2.0])))
+    y = A.spmv(dev(np.ones(3))).cpu().numpy()
+    assert y.tolist() == [1.0, 0.0, 2.0]
+
+
+def test_dia_too_big(mspv):
+    r, c, v = synth.random_coo(200_000, 200_000, 400_000, 5)
+    A = mspv.Matrix.from_coo(200_000, 200_000, dev(r), dev(c), dev(v))
+    with pytest.raises(mspv.MspvError, match="ETOOBIG"):
+        A.convert("dia")
+
+
+def test_memory_cap_injects_enomem(mspv, monkeypatch):
+    r, c, v = synth.random_coo(1000, 1000, 5000, 6)
+    A = mspv.Matrix.from_coo(1000, 1000, r, c, v)
+    monkeypatch.setenv("MSPV_MAX_BYTES", "1000")
+    with pytest.raises(mspv.MspvError, match="ENOMEM"):
+        A.convert("csr")
+    with pytest.raises(mspv.MspvError, match="ENOMEM"):
+        mspv.Matrix.from_coo(1000, 1000, r, c, v)
+    monkeypatch.delenv("MSPV_MAX_BYTES")
+    A.convert("csr")   # works again
