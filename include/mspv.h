@@ -70,7 +70,7 @@ typedef struct {
     int64_t nnz;             /* stored entries (COO/CSR); for DIA the entries it was built from */
     int32_t ndiags;          /* DIA: number of stored diagonals, else 0 */
     int32_t npad;            /* DIA: padded row count of each diagonal (multiple of 32), else 0 */
-    int32_t csr_vector;      /* CSR: lanes per row the SpMV kernel uses (1..32), else 0 */
+    int32_t csr_vector;      /* CSR: 0 = staged row-block kernel, else lanes per row (1..32) */
     int32_t row_max;         /* longest row */
     double row_mean;         /* mean row length */
     double row_std;          /* standard deviation of row lengths */
@@ -181,10 +181,12 @@ MSPV_API const char* mspv_last_error(void);
 MSPV_API const char* mspv_status_string(mspv_status s);
 
 /*
- * Lanes per row used by the CSR SpMV kernel for the given row-length statistics
- * (host only, no device access): the smallest power of two in [2, 32] not below
- * the mean row length; rows longer than 32 entries on average use 32 lanes
- * (a warp per row). MSPV_CSR_VEC overrides it. Exposed for tests and tuning.
+ * CSR SpMV kernel choice for the given row-length statistics (host only, no device
+ * access). 0 selects the staged row-block kernel: a CTA per window of 2048 entries
+ * stages the products of the rows starting in it through shared memory and sums
+ * each row in Algorithm 2's order (used while the mean row length is at most 256).
+ * 32 selects a warp per row (longer rows). MSPV_CSR_VEC (0, 1, 2, 4, 8, 16 or 32)
+ * overrides the choice; 1..16 select V lanes per row. Exposed for tests and tuning.
  */
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max);
 

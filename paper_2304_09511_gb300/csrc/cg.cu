@@ -19,7 +19,22 @@
 
 namespace mspv {
 
-static int64_t vec_grid(int64_t n) {
+// Grid of a grid-stride vector kernel: one full wave of resident CTAs (SM count x
+// CTAs per SM at this kernel's register use), fewer when n is small.
+template <auto Kernel>
+static int64_t wave_grid(int64_t n) {
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, kThreads, 0) != cudaSuccess || b < 1) b = 4;
+        return b;
+    }();
+    int64_t g = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)kNumSMs * per_sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : g;
+}
+
+static int64_t vec_grid(int64_t n) {   // upper bound of every wave_grid() (partials sizing)
     int64_t b = (n + kThreads - 1) / kThreads;
     const int64_t cap = (int64_t)kNumSMs * 8;
     if (b > cap) b = cap;
@@ -94,25 +109,12 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
     if (st->done) return;
     const double alpha = st->alpha;
     double rr = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    for (; i + stride < n; i += 2 * stride) {
-        const int64_t i2 = i + stride;
-        const double x0 = x[i], x1 = x[i2], p0 = p[i], p1 = p[i2];
-        const double r0 = r[i], r1 = r[i2], q0 = q[i], q1 = q[i2];
-        x[i] = fma(alpha, p0, x0);
-        x[i2] = fma(alpha, p1, x1);
-        const double n0 = fma(-alpha, q0, r0), n1 = fma(-alpha, q1, r1);
-        r[i] = n0;
-        r[i2] = n1;
-        rr = fma(n0, n0, rr);
-        rr = fma(n1, n1, rr);
-    }
-    if (i < n) {
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
         x[i] = fma(alpha, p[i], x[i]);
-        const double n0 = fma(-alpha, q[i], r[i]);
-        r[i] = n0;
-        rr = fma(n0, n0, rr);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
     }
     double tot;
     if (last_block_total(rr, partials, &st->ticket, &tot) && threadIdx.x == 0) {
@@ -138,15 +140,9 @@ __global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, const d
                                                               const CgState* st) {
     if (st->done) return;
     const double beta = st->beta;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    for (; i + stride < n; i += 2 * stride) {
-        const int64_t i2 = i + stride;
-        const double r0 = r[i], r1 = r[i2], p0 = p[i], p1 = p[i2];
-        p[i] = fma(beta, p0, r0);
-        p[i2] = fma(beta, p1, r1);
-    }
-    if (i < n) p[i] = fma(beta, p[i], r[i]);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads)
+        p[i] = fma(beta, p[i], r[i]);
 }
 
 // Iterative refinement helpers: r = b - q with rho = r.r (and ||b|| on the first call).
@@ -229,9 +225,12 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
     hst->maxit = maxit;
     MSPV_CUDA_TRY(cudaMemcpyAsync(w.st, hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
     const unsigned G = (unsigned)vec_grid(n);
+    const unsigned Gi = (unsigned)wave_grid<cg_init_kernel>(n);
+    const unsigned Gu = (unsigned)wave_grid<cg_update_kernel>(n);
+    const unsigned Gp = (unsigned)wave_grid<cg_pupdate_kernel>(n);
 
     MSPV_TRY(launch_spmv(A, x, w.q, s, DotEpilogue{nullptr, nullptr}));
-    cg_init_kernel<<<G, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.st);
+    cg_init_kernel<<<Gi, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
@@ -248,8 +247,8 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
         const int32_t batch = std::min<int32_t>(every, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(launch_spmv(A, w.p, w.q, s, ep));
-            cg_update_kernel<<<G, kThreads, 0, s>>>(n, x, w.r, w.p, w.q, w.partials, w.st);
-            cg_pupdate_kernel<<<G, kThreads, 0, s>>>(n, w.r, w.p, w.st);
+            cg_update_kernel<<<Gu, kThreads, 0, s>>>(n, x, w.r, w.p, w.q, w.partials, w.st);
+            cg_pupdate_kernel<<<Gp, kThreads, 0, s>>>(n, w.r, w.p, w.st);
         }
         MSPV_CUDA_TRY(cudaGetLastError());
         launched += batch;

@@ -549,6 +549,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
             }
             MSPV_TRY(exclusive_scan_i32(M->irp, M->irp, M->nrows, M->irp + M->nrows, s));
             M->csr_vector = choose_csr_vector(M->row_mean, M->row_std, M->row_max);
+            MSPV_TRY(build_csr_row_blocks(M, s));
         }
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));
         return MSPV_OK;
@@ -603,7 +604,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
 
 mspv_status ensure_coo_carry(mspv_matrix* M) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
-    M->nchunks = (M->nnz + kCooChunk - 1) / kCooChunk;
+    M->nchunks = (M->nnz + kCooWindow - 1) / kCooWindow;
     MSPV_TRY(dev_alloc_n(&M->carry, M->nchunks > 0 ? M->nchunks : 1));
     M->bytes += (M->nchunks > 0 ? M->nchunks : 1) * (int64_t)sizeof(CooCarry);
     return MSPV_OK;
@@ -640,12 +641,13 @@ mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, do
 
 void free_matrix(mspv_matrix* M) {
     auto f = [](void* p) { if (p) dev_free(p, 0); };
-    f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->av); f(M->carry);
+    f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->av); f(M->carry); f(M->row_block);
     f(M->cg.r); f(M->cg.p); f(M->cg.q); f(M->cg.partials); f(M->cg.st);
     if (M->cg.host_st) cudaFreeHost(M->cg.host_st);
     M->ai = M->aj = M->irp = M->doff = nullptr;
     M->av = nullptr;
     M->carry = nullptr;
+    M->row_block = nullptr;
     M->cg = CgWork{};
 }
 

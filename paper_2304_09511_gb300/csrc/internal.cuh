@@ -75,6 +75,36 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 inline size_t value_size(int vt) { return vt == MSPV_F64 ? 8 : (vt == MSPV_F32 ? 4 : 2); }
 
+// Exact FP32 -> FP64 widening with integer operations only. On GB300 the hardware
+// conversion issues on the (narrow) FP64 pipe at the rate of an FP64 FMA; this costs a
+// handful of integer instructions instead. IEEE binary32 -> binary64 is exact:
+// sign kept, exponent rebiased by 1023 - 127 = 896, mantissa shifted left by 29;
+// subnormals are normalised, infinities and NaNs keep their payload.
+__device__ __forceinline__ double widen_f32_bits(uint32_t u) {
+    const uint32_t sign = u & 0x80000000u;
+    const uint32_t e = (u >> 23) & 0xffu;
+    uint32_t m = u & 0x7fffffu;
+    uint32_t e64;
+    if (e == 0xffu) {
+        e64 = 0x7ffu;
+    } else if (e != 0u) {
+        e64 = e + 896u;
+    } else if (m == 0u) {
+        e64 = 0u;
+    } else {                                   // subnormal: m * 2^-149
+        const int lz = __clz(m) - 8;           // shift that brings the leading 1 to bit 23
+        m = (m << lz) & 0x7fffffu;
+        e64 = 1023u - 126u - (uint32_t)lz;
+    }
+    const uint32_t hi = sign | (e64 << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return widen_f32_bits(__float_as_uint(v)); }
+__device__ __forceinline__ double widen(__nv_bfloat16 v) {
+    return widen_f32_bits((uint32_t)__bfloat16_as_ushort(v) << 16);
+}
+
 // ---------------------------------------------------------------------------
 // CG device state: scalars live on the device so the loop needs no host sync.
 // ---------------------------------------------------------------------------
@@ -103,16 +133,18 @@ struct DotEpilogue {
     double* partials;   // one per CTA of the launch
 };
 
-// COO per-chunk carry record for the segmented SpMV.
+// COO per-window carry record: rows that cross a window boundary leave partial sums.
 struct CooCarry {
     int32_t row_first;
     int32_t row_last;
-    double head;   // partial sum of row_first over the chunk
-    double tail;   // partial sum of row_last over the chunk
+    double head;   // partial sum of row_first over the window
+    double tail;   // partial sum of row_last over the window
 };
 
-constexpr int kCooWarpIters = 8;                 // 32 x 8 = 256 entries per warp chunk
-constexpr int kCooChunk = 32 * kCooWarpIters;
+// Entries per CTA window of the staged COO and CSR kernels: values and gathered x are
+// staged in shared memory (16 B per entry, plus 4 B of row index for COO).
+constexpr int kCooWindow = 3072;
+constexpr int kCsrWindow = 2560;     // a CTA takes the rows that start in its window
 
 // CG workspace, owned by a handle and grown on demand.
 struct CgWork {
@@ -148,7 +180,7 @@ struct mspv_matrix {
     int32_t nrows = 0, ncols = 0;
     int64_t nnz = 0;
     int32_t ndiags = 0, npad = 0;
-    int32_t csr_vector = 0;
+    int32_t csr_vector = 0;   // 0: staged row-block kernel; 1..32: lanes per row
     int32_t row_max = 0;
     double row_mean = 0.0, row_std = 0.0;
     int64_t empty_rows = 0;
@@ -161,8 +193,10 @@ struct mspv_matrix {
     void* av = nullptr;       // values (value_type)
     int64_t av_count = 0;
 
-    mspv::CooCarry* carry = nullptr;   // COO: per-chunk carries
-    int64_t nchunks = 0;
+    mspv::CooCarry* carry = nullptr;   // COO: per-window carries
+    int64_t nchunks = 0;               // COO windows
+    int32_t* row_block = nullptr;      // CSR: first row of each window, nblocks + 1 entries
+    int64_t nblocks = 0;               // CSR windows
 
     mspv::CgWork cg;
     int64_t bytes = 0;        // device bytes held
@@ -189,6 +223,7 @@ mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaSt
                         DotEpilogue ep);
 int64_t spmv_partials_needed(const mspv_matrix* A);   // CTAs of the fused-dot launch
 int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
+mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
 
 // cg.cu
 mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,

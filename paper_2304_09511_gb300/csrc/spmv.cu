@@ -1,22 +1,31 @@
-// SpMV kernels for the three storage formats of Sec. II-B, y = A x in FP64.
+// SpMV kernels for the three storage formats of Sec. II-B, y = A x, FP64 arithmetic.
 //
-//  DIA (Algorithm 3): diagonal-major values, each thread owns RPT consecutive rows
-//      and walks the diagonals in order; value loads are 128-bit (FP64: 2 rows,
-//      FP32: 4 rows, BF16: 8 rows), coalesced and streamed past L1. This is the
-//      row-parallel, diagonal-sequential structure of the paper's outer-loop
-//      vectorisation (Sec. III), with a warp's 32 lanes in place of SVE lanes and the
-//      predicate 0 <= k < N kept per element.
-//  CSR (Algorithm 2): V lanes per row (V in 1..32 from the row-length statistics),
-//      strided accumulation then a butterfly reduction inside the V-lane group.
-//  COO (Algorithm 1): each warp owns a contiguous chunk of 256 sorted entries and
-//      does a segmented shuffle-scan keyed by row -- the GPU counterpart of the
-//      paper's SVE COO kernel, which masks runs of equal row index and reduces them
-//      horizontally. Rows that cross a chunk boundary leave partial sums in a carry
-//      record; a fix-up pass adds them in chunk order. No floating-point atomics,
-//      so y is bit-identical run to run.
+// On GB300 the FP64 pipe, not HBM, is the tighter limit for FP64 SpMV: one FP64 FMA
+// per stored value is about as fast as HBM delivers that value, a warp instruction
+// costs the same however many of its lanes are active, and the FP32 -> FP64
+// conversion instruction issues on the same narrow pipe. Every kernel here therefore
+// spends exactly one lane-dense FMA per value it must multiply, widens FP32/BF16
+// values with integer instructions, and avoids FP64 shuffle reductions.
 //
-// All three can fuse CG's p.q into the epilogue (DotEpilogue): the last CTA to
-// finish reduces the per-CTA partials in index order and forms alpha.
+//  DIA (Algorithm 3): diagonal-major values; each thread owns RPT consecutive rows
+//      (FP64: 2, FP32: 4, BF16: 8, one 128-bit value load per diagonal) and walks the
+//      diagonals in order with the predicate 0 <= k < N -- the row-parallel,
+//      diagonal-sequential structure of the paper's outer-loop SVE vectorisation
+//      (Sec. III), with the lanes of a warp in place of SVE lanes.
+//  CSR (Algorithm 2): a CTA takes the rows that start in a window of ~2560 entries,
+//      stages their values and gathered x[aj] through shared memory with coalesced,
+//      independent loads, then each thread sums one row left to right with FMAs.
+//      Rows longer than 128 entries are reduced by the whole CTA. A V-lanes-per-row
+//      kernel (V = 1..32, warp per row at V = 32) is kept for very long rows.
+//  COO (Algorithm 1): a CTA takes a window of 3072 sorted entries, stages them, finds
+//      the runs of equal row index with a block scan, and sums each run in one
+//      thread -- the segmented reduction over runs of equal row index that the
+//      paper's SVE COO kernel performs with a match mask and a horizontal add. Runs
+//      cut by a window edge leave partial sums in a carry record that a fix-up pass
+//      adds in window order.
+// No floating-point atomics anywhere: y is bit-identical run to run. Each kernel can
+// fuse CG's p.q into its epilogue (DotEpilogue); the last CTA reduces the per-CTA
+// partials in index order and forms alpha.
 #include <climits>
 #include <cstdlib>
 
@@ -24,15 +33,16 @@
 
 namespace mspv {
 
-// ---------------------------------------------------------------------------
-// value loads: one scalar, or RPT consecutive values as one 128-bit load
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double to_f64(double v) { return v; }
-__device__ __forceinline__ double to_f64(float v) { return (double)v; }
-__device__ __forceinline__ double to_f64(__nv_bfloat16 v) {
-    return (double)__uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);
-}
+constexpr int kStageCap = 3072;   // entries staged per CTA (values + gathered x)
+constexpr int kLongRun = 128;     // runs longer than this are reduced by the whole CTA
+constexpr int kMaxLongRuns = kStageCap / (kLongRun + 1) + 1;
+constexpr size_t kCsrSmem = 2 * kStageCap * sizeof(double) + (kStageCap + 1) * sizeof(int32_t);
+constexpr size_t kCooSmem = kCsrSmem + kStageCap * sizeof(int32_t);
+static_assert(kCooWindow <= kStageCap, "COO window must fit the staging buffers");
 
+// ---------------------------------------------------------------------------
+// DIA
+// ---------------------------------------------------------------------------
 template <typename VT> struct DiaVec;
 template <> struct DiaVec<double> {
     static constexpr int RPT = 2;
@@ -44,8 +54,9 @@ template <> struct DiaVec<double> {
 template <> struct DiaVec<float> {
     static constexpr int RPT = 4;
     __device__ __forceinline__ static void load(const float* p, double (&v)[RPT]) {
-        const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        v[0] = widen_f32_bits(t.x); v[1] = widen_f32_bits(t.y);
+        v[2] = widen_f32_bits(t.z); v[3] = widen_f32_bits(t.w);
     }
 };
 template <> struct DiaVec<__nv_bfloat16> {
@@ -55,15 +66,12 @@ template <> struct DiaVec<__nv_bfloat16> {
         const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            v[2 * k] = (double)__uint_as_float(w[k] << 16);
-            v[2 * k + 1] = (double)__uint_as_float(w[k] & 0xffff0000u);
+            v[2 * k] = widen_f32_bits(w[k] << 16);
+            v[2 * k + 1] = widen_f32_bits(w[k] & 0xffff0000u);
         }
     }
 };
 
-// ---------------------------------------------------------------------------
-// DIA
-// ---------------------------------------------------------------------------
 constexpr int kDiaSmemDiags = 256;   // offsets cached in shared memory; more are read from global
 
 template <typename VT>
@@ -92,8 +100,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
                 const int64_t k = k0 + r;
-                const double xv = (k >= 0 && k < n) ? __ldg(x + k) : 0.0;
-                acc[r] = fma(a[r], xv, acc[r]);
+                if (k >= 0 && k < n) acc[r] = fma(a[r], __ldg(x + k), acc[r]);
             }
         }
 #pragma unroll
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// CSR, V lanes per row
+// CSR, V lanes per row (long rows)
 // ---------------------------------------------------------------------------
 template <typename VT, int V>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
@@ -128,17 +135,8 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     double sum = 0.0;
     if (row < nrows) {
         const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
-        int32_t j = s + lane;
-        // two independent accumulators for memory-level parallelism
-        double sum2 = 0.0;
-        for (; j + V < e; j += 2 * V) {
-            const int32_t c0 = __ldcs(aj + j), c1 = __ldcs(aj + j + V);
-            const double a0 = to_f64(__ldcs(av + j)), a1 = to_f64(__ldcs(av + j + V));
-            sum = fma(a0, __ldg(x + c0), sum);
-            sum2 = fma(a1, __ldg(x + c1), sum2);
-        }
-        if (j < e) sum = fma(to_f64(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
-        sum += sum2;
+        for (int32_t j = s + lane; j < e; j += V)
+            sum = fma(widen(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
     }
 #pragma unroll
     for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -152,106 +150,245 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// COO, warp-segmented
+// Staged run-per-thread reduction (CSR and COO)
 // ---------------------------------------------------------------------------
+// Coalesced staging of a window: a_s[k] = av[s+k] widened, x_s[k] = x[aj[s+k]].
+// Several loads per thread are issued before any is used.
 template <typename VT>
-__global__ void __launch_bounds__(kThreads) spmv_coo_kernel(
-    int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
-    const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
-    CooCarry* __restrict__ carry, int64_t nchunks, const CgState* st) {
-    if (st && st->done) return;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int64_t w = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    if (w >= nchunks) return;   // whole warp
-    const int64_t c0 = w * kCooChunk;
-    const int64_t c1 = (c0 + kCooChunk < nnz) ? c0 + kCooChunk : nnz;
-
-    // all loads first, for memory-level parallelism
-    int32_t rr[kCooWarpIters];
-    double pp[kCooWarpIters];
-    {
-        int32_t cc[kCooWarpIters];
-        double aa[kCooWarpIters];
+__device__ __forceinline__ void stage_window(const int32_t* __restrict__ aj,
+                                             const VT* __restrict__ av,
+                                             const double* __restrict__ x, int64_t s, int len,
+                                             double* __restrict__ a_s, double* __restrict__ x_s) {
+    constexpr int U = 4;
+    for (int k0 = threadIdx.x; k0 < len; k0 += U * kThreads) {
+        int32_t c[U];
+        double a[U];
 #pragma unroll
-        for (int it = 0; it < kCooWarpIters; ++it) {
-            const int64_t e = c0 + it * 32 + lane;
-            const bool valid = e < c1;
-            rr[it] = valid ? __ldcs(ai + e) : INT_MAX;
-            cc[it] = valid ? __ldcs(aj + e) : 0;
-            aa[it] = valid ? to_f64(__ldcs(av + e)) : 0.0;
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * kThreads;
+            const bool ok = k < len;
+            c[u] = ok ? __ldcs(aj + s + k) : 0;
+            a[u] = ok ? widen(__ldcs(av + s + k)) : 0.0;
         }
 #pragma unroll
-        for (int it = 0; it < kCooWarpIters; ++it)
-            pp[it] = (rr[it] != INT_MAX) ? aa[it] * __ldg(x + cc[it]) : 0.0;
-    }
-    const int32_t row_first = __shfl_sync(FULL, rr[0], 0);
-    const int32_t row_before = (c0 > 0) ? __ldg(ai + c0 - 1) : -1;
-    const int32_t row_after = (c1 < nnz) ? __ldg(ai + c1) : INT_MAX;
-    const bool cont_prev = (row_before == row_first);
-
-    int32_t carry_row = row_before;
-    double carry_val = 0.0;
-#pragma unroll
-    for (int it = 0; it < kCooWarpIters; ++it) {
-        const int32_t row = rr[it];
-        double v = pp[it];
-        // segmented inclusive scan over equal rows (rows are sorted, so runs are contiguous)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double pv = __shfl_up_sync(FULL, v, o);
-            const int32_t rv = __shfl_up_sync(FULL, row, o);
-            if (lane >= o && rv == row) v += pv;
-        }
-        if (row == carry_row) v += carry_val;
-        int32_t prev_row = __shfl_up_sync(FULL, row, 1);
-        if (lane == 0) prev_row = carry_row;
-        int32_t next_row = __shfl_down_sync(FULL, row, 1);
-        // lane 31 looks at the first entry of the next step; after the last step the
-        // run may continue into the next chunk, which the code after the loop decides
-        const int32_t next_step_row =
-            __shfl_sync(FULL, rr[(it + 1 < kCooWarpIters) ? it + 1 : it], 0);
-        if (lane == 31) next_row = next_step_row;
-        const bool may_end = (lane < 31) || (it + 1 < kCooWarpIters);
-        if (row != INT_MAX) {
-            // rows skipped between the previous entry and this one are empty
-            if (row != prev_row)
-                for (int32_t r = prev_row + 1; r < row; ++r) y[r] = 0.0;
-            if (may_end && next_row != row) {   // the run of `row` ends inside the chunk
-                if (row == row_first && cont_prev) carry[w].head = v;
-                else y[row] = v;                // (such a run never continues past the chunk)
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * kThreads;
+            if (k < len) {
+                a_s[k] = a[u];
+                x_s[k] = __ldg(x + c[u]);
             }
         }
-        carry_row = __shfl_sync(FULL, row, 31);
-        carry_val = __shfl_sync(FULL, v, 31);
-    }
-    if (lane == 0) {
-        int32_t row_last = carry_row;
-        if (carry_row != INT_MAX) {   // the chunk's last entry sits in lane 31 of the last step
-            const bool cont_next = (row_after == carry_row);
-            const bool single = (carry_row == row_first);
-            if (single && cont_prev) carry[w].head = carry_val;
-            if (cont_next) carry[w].tail = carry_val;
-            if (!cont_next && !(single && cont_prev)) y[carry_row] = carry_val;
-        } else {
-            row_last = __ldg(ai + c1 - 1);
-        }
-        carry[w].row_first = row_first;
-        carry[w].row_last = row_last;
-    }
-    if (c1 == nnz) {   // trailing empty rows
-        const int32_t last = __ldg(ai + nnz - 1);
-        for (int32_t r = last + 1 + lane; r < nrows; r += 32) y[r] = 0.0;
     }
 }
 
-// Rows spanning chunks: the chunk where such a row starts adds its tail, the heads of
-// the chunks it covers entirely, and the head of the chunk where it ends, in order.
-__global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_t nchunks,
+// Left-to-right FMA chain over staged entries [b, e).
+__device__ __forceinline__ double run_fma(const double* __restrict__ a_s,
+                                          const double* __restrict__ x_s, int b, int e) {
+    double sum = 0.0;
+    int j = b;
+    for (; j + 4 <= e; j += 4) {
+        sum = fma(a_s[j], x_s[j], sum);
+        sum = fma(a_s[j + 1], x_s[j + 1], sum);
+        sum = fma(a_s[j + 2], x_s[j + 2], sum);
+        sum = fma(a_s[j + 3], x_s[j + 3], sum);
+    }
+    for (; j < e; ++j) sum = fma(a_s[j], x_s[j], sum);
+    return sum;
+}
+
+// Exclusive scan of one int per thread over the CTA; *total gets the sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = (lane < kThreads / 32) ? s_warp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < kThreads / 32) s_warp[lane] = wi - w;
+        if (lane == kThreads / 32 - 1) s_warp[kThreads / 32] = wi;
+    }
+    __syncthreads();
+    const int r = incl - v + s_warp[warp];
+    *total = s_warp[kThreads / 32];
+    __syncthreads();
+    return r;
+}
+
+// Sum every run [rs[i], rs[i+1]) of the staged window, calling emit(i, sum) once per
+// run: runs up to kLongRun entries in one thread each, longer runs by the whole CTA.
+template <typename Emit>
+__device__ __forceinline__ void reduce_runs(const double* __restrict__ a_s,
+                                            const double* __restrict__ x_s,
+                                            const int32_t* __restrict__ rs, int nruns, Emit emit) {
+    __shared__ int s_long[kMaxLongRuns];
+    __shared__ int s_nlong;
+    __shared__ double s_red[32];
+    if (threadIdx.x == 0) s_nlong = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nruns; i += kThreads) {
+        const int b = rs[i], e = rs[i + 1];
+        if (e - b > kLongRun) {
+            s_long[atomicAdd(&s_nlong, 1)] = i;   // processing order only; results unaffected
+            continue;
+        }
+        emit(i, run_fma(a_s, x_s, b, e));
+    }
+    __syncthreads();
+    const int nlong = s_nlong;
+    for (int l = 0; l < nlong; ++l) {
+        const int i = s_long[l];
+        const int b = rs[i], e = rs[i + 1];
+        double part = 0.0;
+        for (int j = b + threadIdx.x; j < e; j += kThreads) part = fma(a_s[j], x_s[j], part);
+        const double sum = block_sum(part, s_red);
+        if (threadIdx.x == 0) emit(i, sum);
+    }
+}
+
+// CSR: CTA b takes rows [row_block[b], row_block[b+1]), the rows whose first entry lies
+// in entry window b. Blocks too large to stage are reduced row by row by the whole CTA.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
+    const int32_t* __restrict__ irp, const int32_t* __restrict__ aj, const VT* __restrict__ av,
+    const int32_t* __restrict__ row_block, const double* __restrict__ x, double* __restrict__ y,
+    DotEpilogue ep) {
+    if (ep.st && ep.st->done) return;
+    extern __shared__ double smem[];
+    double* a_s = smem;
+    double* x_s = a_s + kStageCap;
+    int32_t* rs = reinterpret_cast<int32_t*>(x_s + kStageCap);
+    __shared__ double s_red[32];
+    const int32_t rb = row_block[blockIdx.x], re = row_block[blockIdx.x + 1];
+    const int nr = re - rb;
+    double dot = 0.0;
+    if (nr > 0) {
+        const int32_t s = __ldg(irp + rb), e = __ldg(irp + re);
+        const int len = e - s;
+        if (len <= kStageCap && nr <= kStageCap) {
+            for (int i = threadIdx.x; i <= nr; i += kThreads) rs[i] = __ldg(irp + rb + i) - s;
+            stage_window(aj, av, x, s, len, a_s, x_s);
+            __syncthreads();
+            reduce_runs(a_s, x_s, rs, nr, [&](int i, double sum) {
+                y[rb + i] = sum;
+                if (ep.st) dot = fma(__ldg(x + rb + i), sum, dot);
+            });
+        } else {
+            for (int32_t r = rb; r < re; ++r) {   // uniform over the CTA
+                const int32_t a = __ldg(irp + r), b = __ldg(irp + r + 1);
+                if (a == b) {
+                    if (threadIdx.x == 0) y[r] = 0.0;
+                    continue;
+                }
+                double part = 0.0;
+                for (int32_t j = a + threadIdx.x; j < b; j += kThreads)
+                    part = fma(widen(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
+                const double sum = block_sum(part, s_red);
+                if (threadIdx.x == 0) {
+                    y[r] = sum;
+                    if (ep.st) dot = fma(__ldg(x + r), sum, dot);
+                }
+            }
+        }
+    }
+    if (ep.st) {
+        double tot;
+        if (last_block_total(dot, ep.partials, &ep.st->ticket, &tot) && threadIdx.x == 0)
+            finish_alpha(ep.st, tot);
+    }
+}
+
+// First row of each entry window: row_block[w] = first r in [0, n] with irp[r] >= w*W,
+// for w < nblocks; row_block[nblocks] = n.
+__global__ void csr_row_block_kernel(const int32_t* __restrict__ irp, int32_t n, int64_t nblocks,
+                                     int32_t* __restrict__ row_block) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = (r == 0) ? 0 : (int64_t)irp[r - 1] / kCsrWindow + 1;
+        int64_t hi = (int64_t)irp[r] / kCsrWindow;
+        if (hi > nblocks - 1) hi = nblocks - 1;
+        for (int64_t w = lo; w <= hi; ++w) row_block[w] = (int32_t)r;
+        if (r == n) row_block[nblocks] = n;
+    }
+}
+
+// COO: CTA w takes entries [w*W, (w+1)*W) of the sorted arrays.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
+    int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
+    const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
+    CooCarry* __restrict__ carry, const CgState* st) {
+    if (st && st->done) return;
+    extern __shared__ double smem[];
+    double* a_s = smem;
+    double* x_s = a_s + kStageCap;
+    int32_t* rs = reinterpret_cast<int32_t*>(x_s + kStageCap);
+    int32_t* srow = rs + kStageCap + 1;
+    __shared__ int s_warp[kThreads / 32 + 1];
+    const int64_t w = blockIdx.x;
+    const int64_t s = w * kCooWindow;
+    const int len = (int)((nnz - s < kCooWindow) ? nnz - s : kCooWindow);
+    for (int k = threadIdx.x; k < len; k += kThreads) srow[k] = __ldcs(ai + s + k);
+    stage_window(aj, av, x, s, len, a_s, x_s);
+    const int32_t row_before = (s > 0) ? __ldg(ai + s - 1) : -1;
+    const int32_t row_after = (s + len < nnz) ? __ldg(ai + s + len) : INT_MAX;
+    __syncthreads();
+
+    // run starts: positions whose row differs from the previous entry's
+    const int per = (len + kThreads - 1) / kThreads;
+    const int kb = threadIdx.x * per;
+    const int ke = (kb + per < len) ? kb + per : len;
+    int cnt = 0;
+    for (int k = kb; k < ke; ++k) cnt += (k == 0 || srow[k] != srow[k - 1]);
+    int nruns;
+    int pos = block_excl_scan(cnt, s_warp, &nruns);
+    for (int k = kb; k < ke; ++k)
+        if (k == 0 || srow[k] != srow[k - 1]) rs[pos++] = k;
+    if (threadIdx.x == 0) rs[nruns] = len;
+    __syncthreads();
+
+    const int32_t row_first = srow[0], row_last = srow[len - 1];
+    const bool cont_prev = (row_before == row_first);
+    const bool cont_next = (row_after == row_last);
+    // rows with no entries between consecutive runs (and before the first)
+    for (int i = threadIdx.x; i < nruns; i += kThreads) {
+        const int32_t r = srow[rs[i]];
+        const int32_t prev = (i > 0) ? srow[rs[i] - 1] : row_before;
+        for (int32_t z = prev + 1; z < r; ++z) y[z] = 0.0;
+    }
+    reduce_runs(a_s, x_s, rs, nruns, [&](int i, double sum) {
+        const int32_t r = srow[rs[i]];
+        const bool to_head = (i == 0) && cont_prev;
+        const bool to_tail = (i == nruns - 1) && cont_next;
+        if (to_head) carry[w].head = sum;
+        if (to_tail) carry[w].tail = sum;
+        if (!to_head && !to_tail) y[r] = sum;
+    });
+    if (threadIdx.x == 0) {
+        carry[w].row_first = row_first;
+        carry[w].row_last = row_last;
+    }
+    if (s + len == nnz)   // empty rows after the last entry
+        for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) y[z] = 0.0;
+}
+
+// Rows spanning windows: the window where such a row starts adds its tail, the heads of
+// the windows it covers entirely, and the head of the window where it ends, in order.
+__global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_t nwin,
                                       double* __restrict__ y, const CgState* st) {
     if (st && st->done) return;
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nchunks - 1) return;   // the last chunk cannot continue into another
+    if (w >= nwin - 1) return;   // the last window cannot continue into another
     const CooCarry c = carry[w];
     const bool cont_next = carry[w + 1].row_first == c.row_last;
     const bool single = c.row_first == c.row_last;
@@ -263,7 +400,7 @@ __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_
         const CooCarry d = carry[v];
         sum += d.head;
         const bool d_single = d.row_first == d.row_last;
-        const bool d_next = (v + 1 < nchunks) && carry[v + 1].row_first == d.row_last;
+        const bool d_next = (v + 1 < nwin) && carry[v + 1].row_first == d.row_last;
         if (d_single && d_next) ++v;
         else break;
     }
@@ -298,11 +435,25 @@ int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen) {
     (void)maxlen;
     if (const char* s = std::getenv("MSPV_CSR_VEC")) {
         int v = std::atoi(s);
-        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) return v;
+        if (v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) return v;
     }
-    int v = 2;
-    while (v < 32 && (double)v < mean) v <<= 1;
-    return v;
+    // staged row blocks while rows are short enough for many of them to share a
+    // window; a warp per row once rows average more than a window's worth per warp
+    if (mean <= 256.0) return 0;
+    return 32;
+}
+
+mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s) {
+    M->nblocks = (M->nnz + kCsrWindow - 1) / kCsrWindow;
+    if (M->nblocks < 1) M->nblocks = 1;
+    MSPV_TRY(dev_alloc_n(&M->row_block, M->nblocks + 1));
+    M->bytes += (M->nblocks + 1) * 4;
+    const int64_t threads = (int64_t)M->nrows + 1;
+    unsigned grid = (unsigned)((threads + kThreads - 1) / kThreads);
+    if (grid > (unsigned)kNumSMs * 64) grid = kNumSMs * 64;
+    csr_row_block_kernel<<<grid, kThreads, 0, s>>>(M->irp, M->nrows, M->nblocks, M->row_block);
+    MSPV_CUDA_TRY(cudaGetLastError());
+    return MSPV_OK;
 }
 
 static inline unsigned blocks_for(int64_t threads) {
@@ -323,7 +474,7 @@ int64_t spmv_partials_needed(const mspv_matrix* A) {
             return blocks_for((A->nrows + rpt - 1) / rpt);
         }
         case MSPV_CSR:
-            return blocks_for((int64_t)A->nrows * A->csr_vector);
+            return A->csr_vector == 0 ? A->nblocks : blocks_for((int64_t)A->nrows * A->csr_vector);
         default:
             return vector_grid(A->nrows);
     }
@@ -341,9 +492,19 @@ static void launch_dia(const mspv_matrix* A, const double* x, double* y, cudaStr
 template <typename VT>
 static void launch_csr(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                        DotEpilogue ep) {
-    const int V = A->csr_vector;
-    const unsigned grid = blocks_for((int64_t)A->nrows * V);
     const VT* av = static_cast<const VT*>(A->av);
+    const int V = A->csr_vector;
+    if (V == 0) {
+        static const bool attr = [] {
+            return cudaFuncSetAttribute(spmv_csr_stage_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kCsrSmem) == cudaSuccess;
+        }();
+        (void)attr;
+        spmv_csr_stage_kernel<VT><<<(unsigned)A->nblocks, kThreads, kCsrSmem, s>>>(A->irp, A->aj, av,
+                                                                                   A->row_block, x, y, ep);
+        return;
+    }
+    const unsigned grid = blocks_for((int64_t)A->nrows * V);
 #define MSPV_CSR_CASE(VV)                                                                 \
     case VV:                                                                              \
         spmv_csr_vector_kernel<VT, VV><<<grid, kThreads, 0, s>>>(A->nrows, A->irp, A->aj, \
@@ -365,8 +526,13 @@ template <typename VT>
 static void launch_coo(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                        DotEpilogue ep) {
     const VT* av = static_cast<const VT*>(A->av);
-    spmv_coo_kernel<VT><<<blocks_for(A->nchunks * 32), kThreads, 0, s>>>(
-        A->nrows, A->nnz, A->ai, A->aj, av, x, y, A->carry, A->nchunks, ep.st);
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(spmv_coo_stage_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kCooSmem) == cudaSuccess;
+    }();
+    (void)attr;
+    spmv_coo_stage_kernel<VT><<<(unsigned)A->nchunks, kThreads, kCooSmem, s>>>(
+        A->nrows, A->nnz, A->ai, A->aj, av, x, y, A->carry, ep.st);
     if (A->nchunks > 1)
         spmv_coo_fixup_kernel<<<blocks_for(A->nchunks), kThreads, 0, s>>>(A->carry, A->nchunks, y, ep.st);
     if (ep.st)

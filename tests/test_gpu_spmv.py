@@ -123,8 +123,8 @@ def test_banded_structure_and_spmv(mspv, orc, case, fmt):
     assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), O, x, orc)
 
 
-@pytest.mark.parametrize("vec", [1, 2, 4, 8, 16, 32])
-def test_csr_every_vector_width(mspv, orc, vec, monkeypatch):
+@pytest.mark.parametrize("vec", [0, 1, 2, 4, 8, 16, 32])
+def test_csr_every_kernel_choice(mspv, orc, vec, monkeypatch):
     monkeypatch.setenv("MSPV_CSR_VEC", str(vec))
     case = (3000, 3000, 60_000, 21, 0.0, 30)
     A, O = build_pair(mspv, orc, case, True)
@@ -132,6 +132,30 @@ def test_csr_every_vector_width(mspv, orc, vec, monkeypatch):
     assert C.info["csr_vector"] == vec
     x = synth.uniform_x(case[1], 5)
     assert_spmv_parity(C.spmv(dev(x)).cpu().numpy(), orc.coo_to_csr(O), x, orc)
+    # long rows: a block too large to stage takes the whole-CTA path
+    r = np.concatenate([np.full(9000, 7), np.full(5000, 2999), np.arange(3000)]).astype(np.int32)
+    c = np.random.default_rng(2).integers(0, 3000, r.size).astype(np.int32)
+    v = np.random.default_rng(3).uniform(-1, 1, r.size)
+    L = mspv.Matrix.from_coo(3000, 3000, dev(r), dev(c), dev(v)).convert("csr")
+    OL = orc.coo_to_csr(orc.canonicalize(3000, 3000, r, c, v))
+    assert_spmv_parity(L.spmv(dev(x)).cpu().numpy(), OL, x, orc)
+
+
+def test_window_edges_of_staged_kernels(mspv, orc):
+    """Rows cut by COO window edges (every 3072 entries) and CSR row blocks of every size
+    agree with the oracle: long rows span several windows, short rows straddle edges."""
+    n = 9000
+    rng = np.random.default_rng(12)
+    lens = rng.choice([1, 2, 27, 130, 3071, 3072, 3073, 7000], size=60)
+    rows = np.repeat(rng.choice(n, 60, replace=False), lens)
+    cols = rng.integers(0, n, rows.size)
+    vals = rng.uniform(-1, 1, rows.size)
+    A = mspv.Matrix.from_coo(n, n, dev(rows.astype(np.int32)), dev(cols.astype(np.int32)), dev(vals))
+    O = orc.canonicalize(n, n, rows, cols, vals)
+    x = synth.uniform_x(n, 8) * 2 - 1
+    for fmt in ("coo", "csr"):
+        M = A if fmt == "coo" else A.convert(fmt)
+        assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), orc.convert(O, fmt), x, orc)
 
 
 def test_long_rows_and_chunk_spanning(mspv, orc):
