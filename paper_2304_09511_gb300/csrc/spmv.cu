@@ -36,9 +36,11 @@ namespace mspv {
 constexpr int kStageCap = 3072;   // entries staged per CTA (values + gathered x)
 constexpr int kLongRun = 128;     // runs longer than this are reduced by the whole CTA
 constexpr int kMaxLongRuns = kStageCap / (kLongRun + 1) + 1;
-constexpr size_t kCsrSmem = 2 * kStageCap * sizeof(double) + (kStageCap + 1) * sizeof(int32_t);
+constexpr int kRsCap = kStageCap + 4;   // run starts (+1 sentinel), padded so srow stays 16-byte aligned
+constexpr size_t kCsrSmem = 2 * kStageCap * sizeof(double) + kRsCap * sizeof(int32_t);
 constexpr size_t kCooSmem = kCsrSmem + kStageCap * sizeof(int32_t);
 static_assert(kCooWindow <= kStageCap, "COO window must fit the staging buffers");
+static_assert((2 * kStageCap * sizeof(double) + kRsCap * sizeof(int32_t)) % 16 == 0, "srow alignment");
 
 // ---------------------------------------------------------------------------
 // DIA
@@ -152,47 +154,64 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
 // ---------------------------------------------------------------------------
 // Staged run-per-thread reduction (CSR and COO)
 // ---------------------------------------------------------------------------
-// Coalesced staging of a window: a_s[k] = av[s+k] widened, x_s[k] = x[aj[s+k]].
-// Several loads per thread are issued before any is used.
+// Asynchronous global -> shared copies (LDGSTS). Completion is awaited with
+// cp.async.wait_group, a hardware wait on the issuing thread's own copies.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Value slot k of the staging buffer: FP64 values are staged as is, FP32 values as
+// their 4 raw bytes (widened when read), BF16 values already widened.
+template <typename VT> struct Staged {
+    __device__ __forceinline__ static double get(const double* a_s, int k) { return a_s[k]; }
+};
+template <> struct Staged<float> {
+    __device__ __forceinline__ static double get(const double* a_s, int k) {
+        return widen_f32_bits(reinterpret_cast<const uint32_t*>(a_s + k)[0]);
+    }
+};
+
+// Stage a window: a_s[k] = av[s+k], x_s[k] = x[aj[s+k]]. Every copy of a phase is in
+// flight at once: first the values and column indices (the index lands in x_s[k]'s
+// slot), then, per thread and for its own slots only, the gathers of x.
 template <typename VT>
 __device__ __forceinline__ void stage_window(const int32_t* __restrict__ aj,
                                              const VT* __restrict__ av,
                                              const double* __restrict__ x, int64_t s, int len,
                                              double* __restrict__ a_s, double* __restrict__ x_s) {
-    constexpr int U = 4;
-    for (int k0 = threadIdx.x; k0 < len; k0 += U * kThreads) {
-        int32_t c[U];
-        double a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * kThreads;
-            const bool ok = k < len;
-            c[u] = ok ? __ldcs(aj + s + k) : 0;
-            a[u] = ok ? widen(__ldcs(av + s + k)) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * kThreads;
-            if (k < len) {
-                a_s[k] = a[u];
-                x_s[k] = __ldg(x + c[u]);
-            }
-        }
+    int32_t* slot_idx = reinterpret_cast<int32_t*>(x_s);   // aj of entry k at int index 2k
+    for (int k = threadIdx.x; k < len; k += kThreads) {
+        if constexpr (sizeof(VT) == 8) cp_async8(a_s + k, av + s + k);
+        else if constexpr (sizeof(VT) == 4) cp_async4(a_s + k, av + s + k);
+        else a_s[k] = widen(__ldcs(av + s + k));
+        cp_async4(slot_idx + 2 * k, aj + s + k);
     }
+    cp_async_wait_all();
+    for (int k = threadIdx.x; k < len; k += kThreads) cp_async8(x_s + k, x + slot_idx[2 * k]);
+    cp_async_wait_all();
 }
 
 // Left-to-right FMA chain over staged entries [b, e).
+template <typename VT>
 __device__ __forceinline__ double run_fma(const double* __restrict__ a_s,
                                           const double* __restrict__ x_s, int b, int e) {
     double sum = 0.0;
     int j = b;
     for (; j + 4 <= e; j += 4) {
-        sum = fma(a_s[j], x_s[j], sum);
-        sum = fma(a_s[j + 1], x_s[j + 1], sum);
-        sum = fma(a_s[j + 2], x_s[j + 2], sum);
-        sum = fma(a_s[j + 3], x_s[j + 3], sum);
+        sum = fma(Staged<VT>::get(a_s, j), x_s[j], sum);
+        sum = fma(Staged<VT>::get(a_s, j + 1), x_s[j + 1], sum);
+        sum = fma(Staged<VT>::get(a_s, j + 2), x_s[j + 2], sum);
+        sum = fma(Staged<VT>::get(a_s, j + 3), x_s[j + 3], sum);
     }
-    for (; j < e; ++j) sum = fma(a_s[j], x_s[j], sum);
+    for (; j < e; ++j) sum = fma(Staged<VT>::get(a_s, j), x_s[j], sum);
     return sum;
 }
 
@@ -227,7 +246,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
 
 // Sum every run [rs[i], rs[i+1]) of the staged window, calling emit(i, sum) once per
 // run: runs up to kLongRun entries in one thread each, longer runs by the whole CTA.
-template <typename Emit>
+template <typename VT, typename Emit>
 __device__ __forceinline__ void reduce_runs(const double* __restrict__ a_s,
                                             const double* __restrict__ x_s,
                                             const int32_t* __restrict__ rs, int nruns, Emit emit) {
@@ -242,7 +261,7 @@ __device__ __forceinline__ void reduce_runs(const double* __restrict__ a_s,
             s_long[atomicAdd(&s_nlong, 1)] = i;   // processing order only; results unaffected
             continue;
         }
-        emit(i, run_fma(a_s, x_s, b, e));
+        emit(i, run_fma<VT>(a_s, x_s, b, e));
     }
     __syncthreads();
     const int nlong = s_nlong;
@@ -250,7 +269,8 @@ __device__ __forceinline__ void reduce_runs(const double* __restrict__ a_s,
         const int i = s_long[l];
         const int b = rs[i], e = rs[i + 1];
         double part = 0.0;
-        for (int j = b + threadIdx.x; j < e; j += kThreads) part = fma(a_s[j], x_s[j], part);
+        for (int j = b + threadIdx.x; j < e; j += kThreads)
+            part = fma(Staged<VT>::get(a_s, j), x_s[j], part);
         const double sum = block_sum(part, s_red);
         if (threadIdx.x == 0) emit(i, sum);
     }
@@ -264,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
     const int32_t* __restrict__ row_block, const double* __restrict__ x, double* __restrict__ y,
     DotEpilogue ep) {
     if (ep.st && ep.st->done) return;
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     double* a_s = smem;
     double* x_s = a_s + kStageCap;
     int32_t* rs = reinterpret_cast<int32_t*>(x_s + kStageCap);
@@ -279,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
             for (int i = threadIdx.x; i <= nr; i += kThreads) rs[i] = __ldg(irp + rb + i) - s;
             stage_window(aj, av, x, s, len, a_s, x_s);
             __syncthreads();
-            reduce_runs(a_s, x_s, rs, nr, [&](int i, double sum) {
+            reduce_runs<VT>(a_s, x_s, rs, nr, [&](int i, double sum) {
                 y[rb + i] = sum;
                 if (ep.st) dot = fma(__ldg(x + rb + i), sum, dot);
             });
@@ -329,31 +349,48 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
     CooCarry* __restrict__ carry, const CgState* st) {
     if (st && st->done) return;
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     double* a_s = smem;
     double* x_s = a_s + kStageCap;
     int32_t* rs = reinterpret_cast<int32_t*>(x_s + kStageCap);
-    int32_t* srow = rs + kStageCap + 1;
+    int32_t* srow = rs + kRsCap;
     __shared__ int s_warp[kThreads / 32 + 1];
     const int64_t w = blockIdx.x;
     const int64_t s = w * kCooWindow;
     const int len = (int)((nnz - s < kCooWindow) ? nnz - s : kCooWindow);
-    for (int k = threadIdx.x; k < len; k += kThreads) srow[k] = __ldcs(ai + s + k);
+    for (int k = threadIdx.x; k < len; k += kThreads) cp_async4(srow + k, ai + s + k);
     stage_window(aj, av, x, s, len, a_s, x_s);
     const int32_t row_before = (s > 0) ? __ldg(ai + s - 1) : -1;
     const int32_t row_after = (s + len < nnz) ? __ldg(ai + s + len) : INT_MAX;
     __syncthreads();
 
-    // run starts: positions whose row differs from the previous entry's
-    const int per = (len + kThreads - 1) / kThreads;
-    const int kb = threadIdx.x * per;
-    const int ke = (kb + per < len) ? kb + per : len;
-    int cnt = 0;
-    for (int k = kb; k < ke; ++k) cnt += (k == 0 || srow[k] != srow[k - 1]);
+    // run starts: positions whose row differs from the previous entry's. Thread t scans
+    // the PER entries [t*PER, t*PER + PER) with 128-bit shared loads (48-byte stride:
+    // conflict-free per quarter warp).
+    constexpr int PER = kCooWindow / kThreads;
+    static_assert(PER % 4 == 0, "compaction reads four rows at a time");
+    const int kb = threadIdx.x * PER;
+    int32_t rv[PER];
+#pragma unroll
+    for (int q = 0; q < PER / 4; ++q) {
+        const int4 t4 = reinterpret_cast<const int4*>(srow + kb)[q];
+        rv[4 * q] = t4.x; rv[4 * q + 1] = t4.y; rv[4 * q + 2] = t4.z; rv[4 * q + 3] = t4.w;
+    }
+    const int32_t before = (kb > 0 && kb <= len) ? srow[kb - 1] : INT_MIN;
+    unsigned flags = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int k = kb + q;
+        const int32_t prv = (q == 0) ? before : rv[q - 1];
+        if (k < len && (k == 0 || rv[q] != prv)) flags |= 1u << q;
+    }
     int nruns;
-    int pos = block_excl_scan(cnt, s_warp, &nruns);
-    for (int k = kb; k < ke; ++k)
-        if (k == 0 || srow[k] != srow[k - 1]) rs[pos++] = k;
+    int pos = block_excl_scan(__popc(flags), s_warp, &nruns);
+    while (flags) {
+        const int q = __ffs(flags) - 1;
+        flags &= flags - 1;
+        rs[pos++] = kb + q;
+    }
     if (threadIdx.x == 0) rs[nruns] = len;
     __syncthreads();
 
@@ -366,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
         const int32_t prev = (i > 0) ? srow[rs[i] - 1] : row_before;
         for (int32_t z = prev + 1; z < r; ++z) y[z] = 0.0;
     }
-    reduce_runs(a_s, x_s, rs, nruns, [&](int i, double sum) {
+    reduce_runs<VT>(a_s, x_s, rs, nruns, [&](int i, double sum) {
         const int32_t r = srow[rs[i]];
         const bool to_head = (i == 0) && cont_prev;
         const bool to_tail = (i == nruns - 1) && cont_next;
