@@ -158,6 +158,27 @@ MSPV_API mspv_status mspv_cg_solve_ir(mspv_matrix_t A64, mspv_matrix_t Alo, cons
                                       int32_t* outer_iters, int32_t* inner_iters,
                                       double* relres);
 
+/*
+ * COO SpMV y = A x that allocates no device memory (the paper has no counterpart; this
+ * is a library convenience). For callers that cannot call cudaMalloc: applications
+ * whose device memory is reserved up front or strictly budgeted by their own
+ * allocator (for example a framework's caching allocator holding the free memory),
+ * where one more allocation would fail or break the budget.
+ * rows/cols/vals are DEVICE arrays of nnz triplets with row indices non-decreasing
+ * (any column order, duplicates allowed: they are summed); x has ncols and y nrows
+ * device FP64 entries. The per-window scratch of the COO kernel lives in a fixed
+ * 1.5 MiB device array compiled into the library, present on every GPU that loads it
+ * until the process exits; nnz above 201,326,592 (65,536 windows of 3,072 entries)
+ * returns ETOOBIG. EINVAL for an index outside the shape or decreasing rows (checked on
+ * the device; the call synchronises `stream` once to read the check). The first call on
+ * a device looks up the array's device address (call it once before any stream
+ * capture). All calls share the array: calls that overlap on the GPU race on it.
+ */
+MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t ncols, int64_t nnz,
+                                           const int32_t* rows, const int32_t* cols,
+                                           const double* vals, const double* x, double* y,
+                                           void* stream);
+
 /* Fill *info with the handle's shape, format and row statistics. */
 MSPV_API mspv_status mspv_info(mspv_matrix_t A, mspv_matrix_info* info);
 

@@ -21,7 +21,8 @@ import numpy as np
 from . import _lib
 from ._lib import MspvError, FORMATS, VALUE_TYPES, load
 
-__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "stream_handle"]
+__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "stream_handle",
+           "spmv_coo_noalloc"]
 
 _FMT_NAMES = {v: k for k, v in FORMATS.items()}
 _VT_NAMES = {v: k for k, v in VALUE_TYPES.items()}
@@ -39,6 +40,23 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         return a.ctypes.data, 0
     return int(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+def spmv_coo_noalloc(nrows: int, ncols: int, rows, cols, vals, x, y, stream=None):
+    """y = A x for row-sorted COO triplets already on the device (int32 rows/cols,
+    float64 vals, CUDA tensors), without any device allocation by the library: the
+    kernel's scratch is a fixed array compiled into libmspv.so (at most 201,326,592
+    entries). For callers that cannot allocate device memory. Synchronises the stream
+    once to validate the indices."""
+    for t, dt in ((rows, "int32"), (cols, "int32"), (vals, "float64")):
+        if not (t.is_cuda and str(t.dtype).endswith(dt) and t.is_contiguous()):
+            raise TypeError("triplets must be contiguous CUDA tensors (int32, int32, float64)")
+    _check_vec(x, ncols)
+    _check_vec(y, nrows)
+    _lib.check(load().mspv_spmv_coo_noalloc(nrows, ncols, int(rows.numel()), rows.data_ptr(),
+                                            cols.data_ptr(), vals.data_ptr(), x.data_ptr(),
+                                            y.data_ptr(), stream_handle(stream)))
+    return y
 
 
 def csr_vector_width(row_mean: float, row_std: float = 0.0, row_max: int = 0) -> int:

@@ -222,6 +222,9 @@ mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
 mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                         DotEpilogue ep);
 int64_t spmv_partials_needed(const mspv_matrix* A);   // CTAs of the fused-dot launch
+mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* aj,
+                           const double* av, const double* x, double* y, CooCarry* carry,
+                           cudaStream_t s);
 int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
 

@@ -576,6 +576,31 @@ static void launch_coo(const mspv_matrix* A, const double* x, double* y, cudaStr
         dot_alpha_kernel<<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(A->nrows, x, y, ep);
 }
 
+// COO SpMV on raw, row-sorted FP64 device triplets with caller-provided carry records
+// (one per 3072-entry window); used by the allocation-free entry point.
+mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* aj,
+                           const double* av, const double* x, double* y, CooCarry* carry,
+                           cudaStream_t s) {
+    if (nrows == 0) return MSPV_OK;
+    if (nnz == 0) {
+        fill_zero_kernel<<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows);
+        MSPV_CUDA_TRY(cudaGetLastError());
+        return MSPV_OK;
+    }
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(spmv_coo_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kCooSmem) == cudaSuccess;
+    }();
+    (void)attr;
+    const int64_t nwin = (nnz + kCooWindow - 1) / kCooWindow;
+    spmv_coo_stage_kernel<double><<<(unsigned)nwin, kThreads, kCooSmem, s>>>(nrows, nnz, ai, aj, av, x, y,
+                                                                            carry, nullptr);
+    if (nwin > 1)
+        spmv_coo_fixup_kernel<<<blocks_for(nwin), kThreads, 0, s>>>(carry, nwin, y, nullptr);
+    MSPV_CUDA_TRY(cudaGetLastError());
+    return MSPV_OK;
+}
+
 mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                         DotEpilogue ep) {
     if (A->nrows == 0) return MSPV_OK;
