@@ -76,22 +76,26 @@ template <> struct DiaVec<__nv_bfloat16> {
 
 constexpr int kDiaSmemDiags = 256;   // offsets cached in shared memory; more are read from global
 
+// One wave of CTAs, each owning the contiguous rows [blockIdx.x * rows_per_cta, ...):
+// every CTA gets the same work, so no SM idles through a partial last wave.
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
     const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
-    DotEpilogue ep) {
+    int64_t rows_per_cta, DotEpilogue ep) {
     constexpr int RPT = DiaVec<VT>::RPT;
     if (ep.st && ep.st->done) return;   // uniform: CG already finished
     __shared__ int32_t s_off[kDiaSmemDiags];
     for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
     __syncthreads();
 
-    const int64_t i0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * RPT;
-    double acc[RPT];
+    const int64_t row0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t row1 = (row0 + rows_per_cta < n) ? row0 + rows_per_cta : n;
+    double d = 0.0;
+    for (int64_t i0 = row0 + (int64_t)threadIdx.x * RPT; i0 < row1; i0 += (int64_t)kThreads * RPT) {
+        double acc[RPT];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) acc[r] = 0.0;
-    if (i0 < n) {
+        for (int r = 0; r < RPT; ++r) acc[r] = 0.0;
         const VT* col = av + i0;
 #pragma unroll 3
         for (int j = 0; j < ndiags; ++j) {
@@ -106,16 +110,14 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
             }
         }
 #pragma unroll
-        for (int r = 0; r < RPT; ++r)
-            if (i0 + r < n) y[i0 + r] = acc[r];
+        for (int r = 0; r < RPT; ++r) {
+            if (i0 + r < n) {
+                y[i0 + r] = acc[r];
+                if (ep.st) d = fma(__ldg(x + i0 + r), acc[r], d);
+            }
+        }
     }
     if (ep.st) {
-        double d = 0.0;
-        if (i0 < n) {
-#pragma unroll
-            for (int r = 0; r < RPT; ++r)
-                if (i0 + r < n) d = fma(__ldg(x + i0 + r), acc[r], d);
-        }
         double tot;
         if (last_block_total(d, ep.partials, &ep.st->ticket, &tot) && threadIdx.x == 0)
             finish_alpha(ep.st, tot);
@@ -504,11 +506,37 @@ static int64_t vector_grid(int64_t n) {
     return b < 1 ? 1 : b;
 }
 
+// DIA launch shape: G CTAs (at most one wave of resident CTAs), each owning an equal,
+// 8-row-aligned range of rows (8 keeps every 128-bit value load aligned).
+template <typename VT>
+static void dia_shape(int32_t n, int64_t* grid, int64_t* rows_per_cta) {
+    constexpr int RPT = DiaVec<VT>::RPT;
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, spmv_dia_kernel<VT>, kThreads, 0) != cudaSuccess ||
+            b < 1)
+            b = 4;
+        return b;
+    }();
+    int64_t g = ((int64_t)n + (int64_t)kThreads * RPT - 1) / ((int64_t)kThreads * RPT);
+    const int64_t wave = (int64_t)kNumSMs * per_sm;
+    if (g > wave) g = wave;
+    if (g < 1) g = 1;
+    int64_t r = ((int64_t)n + g - 1) / g;
+    r = (r + 7) / 8 * 8;
+    *grid = ((int64_t)n + r - 1) / r;
+    if (*grid < 1) *grid = 1;
+    *rows_per_cta = r;
+}
+
 int64_t spmv_partials_needed(const mspv_matrix* A) {
     switch (A->format) {
         case MSPV_DIA: {
-            const int rpt = A->value_type == MSPV_F64 ? 2 : (A->value_type == MSPV_F32 ? 4 : 8);
-            return blocks_for((A->nrows + rpt - 1) / rpt);
+            int64_t grid, rows;
+            if (A->value_type == MSPV_F64) dia_shape<double>(A->nrows, &grid, &rows);
+            else if (A->value_type == MSPV_F32) dia_shape<float>(A->nrows, &grid, &rows);
+            else dia_shape<__nv_bfloat16>(A->nrows, &grid, &rows);
+            return grid;
         }
         case MSPV_CSR:
             return A->csr_vector == 0 ? A->nblocks : blocks_for((int64_t)A->nrows * A->csr_vector);
@@ -520,10 +548,10 @@ int64_t spmv_partials_needed(const mspv_matrix* A) {
 template <typename VT>
 static void launch_dia(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                        DotEpilogue ep) {
-    constexpr int RPT = DiaVec<VT>::RPT;
-    const unsigned grid = blocks_for((A->nrows + RPT - 1) / RPT);
-    spmv_dia_kernel<VT><<<grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
-                                                  static_cast<const VT*>(A->av), x, y, ep);
+    int64_t grid, rows;
+    dia_shape<VT>(A->nrows, &grid, &rows);
+    spmv_dia_kernel<VT><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
+                                                            static_cast<const VT*>(A->av), x, y, rows, ep);
 }
 
 template <typename VT>
