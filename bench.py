@@ -160,6 +160,7 @@ def run_mspv(args, world, rank, local):
     D = A.convert("dia")
     t_dia = time.perf_counter() - t0
     D32 = A.convert("dia", "f32")
+    D16 = A.convert("dia", "bf16")
     del rows, cols, vals
     ndiags = D.info["ndiags"]
     bm = byte_model(n, nnz, ndiags)
@@ -263,9 +264,18 @@ def run_mspv(args, world, rank, local):
 
     # CG time-to-1e-10 (FP64 DIA) and mixed precision (FP32 DIA values, FP64 refinement)
     tt = {}
-    for label, fn in (("fp64", lambda xx: D.cg(b, x=xx, tol=1e-10, maxit=5000)),
-                      ("mixed_f32_ir", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=1e-5,
-                                                          max_outer=20, maxit_inner=5000))):
+    modes = (
+        ("fp64", lambda xx: D.cg(b, x=xx, tol=1e-10, maxit=5000)),
+        # FP32 values, FP64 arithmetic in the inner CG (as the mixed-precision target specifies)
+        ("ir_f32_values_fp64_inner", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=1e-5,
+                                                        max_outer=20, maxit_inner=5000)),
+        # FP32 / BF16 values with an FP32-arithmetic inner CG
+        ("ir_f32_values_fp32_inner", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=args.ir_inner_tol,
+                                                        max_outer=30, maxit_inner=5000, inner_fp32=True)),
+        ("ir_bf16_values_fp32_inner", lambda xx: D.cg_ir(D16, b, x=xx, tol=1e-10, inner_tol=args.ir_inner_tol,
+                                                         max_outer=30, maxit_inner=5000, inner_fp32=True)),
+    )
+    for label, fn in modes:
         os.environ["MSPV_CG_CHECK_EVERY"] = "10"
         xx = torch.zeros(n, dtype=torch.float64, device=dev)
         fn(xx)   # warm
@@ -396,6 +406,8 @@ def main():
     ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
     ap.add_argument("--cpu-cg-iters", type=int, default=100,
                     help="CG iterations in the CPU-baseline sample (GPU arm)")
+    ap.add_argument("--ir-inner-tol", type=float, default=1e-4,
+                    help="inner tolerance of the FP32-arithmetic refinement")
     ap.add_argument("--ref-cg-iters", type=int, default=1,
                     help="CG iterations per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -147,15 +147,22 @@ MSPV_API mspv_status mspv_cg_solve(mspv_matrix_t A, const double* b, double* x, 
  * Mixed-precision CG with iterative refinement (not in the paper). A64 and Alo hold
  * the same matrix; Alo typically stores FP32 or BF16 values (any format). Outer loop
  * in FP64 on A64: r = b - A64 x; stop when ||r|| / ||b|| <= tol; otherwise solve
- * Alo d = r by mspv_cg_solve's iteration from d = 0 to relative tolerance inner_tol
- * (at most maxit_inner iterations), then x += d. At most max_outer corrections.
+ * Alo d = r approximately from d = 0 to relative tolerance inner_tol (at most
+ * maxit_inner iterations), then x += d. At most max_outer corrections.
+ * inner_fp32 = 0: the inner CG is mspv_cg_solve's FP64 iteration on Alo (values widened
+ *   exactly, FP64 FMAs and vectors).
+ * inner_fp32 = 1: the inner CG runs in FP32 arithmetic (FP32 vectors and FMAs) on the
+ *   unit-norm right-hand side r / ||r||, with alpha, beta, rho and the cross-CTA sums of
+ *   every dot product kept in FP64; x += ||r|| d in FP64. Alo must store FP32 or BF16
+ *   values (EFORMAT otherwise). On GB300, whose FP64 pipe is ~1/64 of its FP32 pipe,
+ *   this is the mode that makes refinement faster than plain FP64 CG.
  * Outputs (host, may be NULL): *outer_iters, *inner_iters (sum over corrections),
  * *relres = final ||b - A64 x|| / ||b||. Returns OK, ENOTCONV or EBREAKDOWN.
  */
 MSPV_API mspv_status mspv_cg_solve_ir(mspv_matrix_t A64, mspv_matrix_t Alo, const double* b,
                                       double* x, double tol, double inner_tol,
-                                      int32_t max_outer, int32_t maxit_inner, void* stream,
-                                      int32_t* outer_iters, int32_t* inner_iters,
+                                      int32_t max_outer, int32_t maxit_inner, int32_t inner_fp32,
+                                      void* stream, int32_t* outer_iters, int32_t* inner_iters,
                                       double* relres);
 
 /*

@@ -181,8 +181,10 @@ class Matrix:
         return CgResult(x, st, it.value, rr.value)
 
     def cg_ir(self, low: "Matrix", b, x=None, tol: float = 1e-10, inner_tol: float = 1e-6,
-              max_outer: int = 50, maxit_inner: int = 10000, stream=None) -> CgResult:
-        """Iterative refinement: FP64 residuals on self, inner CG on `low` (e.g. BF16 values)."""
+              max_outer: int = 50, maxit_inner: int = 10000, inner_fp32: bool = False,
+              stream=None) -> CgResult:
+        """Iterative refinement: FP64 residuals on self, inner CG on `low` (e.g. BF16 values),
+        in FP64 arithmetic or (inner_fp32=True) in FP32 arithmetic."""
         import torch
         n = self.shape[0]
         _check_vec(b, n)
@@ -191,7 +193,7 @@ class Matrix:
         _check_vec(x, n)
         oi, ii, rr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
         st = load().mspv_cg_solve_ir(self._h, low._h, b.data_ptr(), x.data_ptr(), float(tol),
-                                     float(inner_tol), int(max_outer), int(maxit_inner),
+                                     float(inner_tol), int(max_outer), int(maxit_inner), int(bool(inner_fp32)),
                                      stream_handle(stream), ctypes.byref(oi), ctypes.byref(ii),
                                      ctypes.byref(rr))
         _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))

@@ -44,7 +44,7 @@ SIGNATURES = {
     "mspv_convert": (i32, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
     "mspv_spmv": (i32, [vp, vp, vp, vp]),
     "mspv_cg_solve": (i32, [vp, vp, vp, dbl, i32, vp, P_I32, P_DBL]),
-    "mspv_cg_solve_ir": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, P_I32, P_I32, P_DBL]),
+    "mspv_cg_solve_ir": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp, P_I32, P_I32, P_DBL]),
     "mspv_spmv_coo_noalloc": (i32, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
     "mspv_info": (i32, [vp, ctypes.POINTER(MatrixInfo)]),
     "mspv_export": (i32, [vp, vp, vp, vp, vp]),

@@ -226,13 +226,13 @@ MSPV_API mspv_status mspv_cg_solve(mspv_matrix_t A, const double* b, double* x, 
 
 MSPV_API mspv_status mspv_cg_solve_ir(mspv_matrix_t A64, mspv_matrix_t Alo, const double* b, double* x,
                                       double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
-                                      void* stream, int32_t* outer_iters, int32_t* inner_iters,
-                                      double* relres) {
+                                      int32_t inner_fp32, void* stream, int32_t* outer_iters,
+                                      int32_t* inner_iters, double* relres) {
     MSPV_GUARD_BEGIN
     if (!A64 || !Alo) return set_error(MSPV_EINVAL, "cg_ir: NULL matrix");
     if ((!b || !x) && A64->nrows > 0) return set_error(MSPV_EINVAL, "cg_ir: NULL vector");
-    return cg_solve_ir(A64, Alo, b, x, tol, inner_tol, max_outer, maxit_inner, as_stream(stream),
-                       outer_iters, inner_iters, relres);
+    return cg_solve_ir(A64, Alo, b, x, tol, inner_tol, max_outer, maxit_inner, inner_fp32,
+                       as_stream(stream), outer_iters, inner_iters, relres);
     MSPV_GUARD_END
 }
 

@@ -44,7 +44,7 @@ static int64_t vec_grid(int64_t n) {   // upper bound of every wave_grid() (part
 // Two fused sums reduced by the last CTA (partials holds 2 per CTA).
 __device__ __forceinline__ bool last_block_total2(double a, double b, double* partials,
                                                   uint32_t* ticket, double* ta, double* tb) {
-    __shared__ double s_red[32];
+    __shared__ double s_red[kThreads];
     __shared__ bool s_last;
     const double sa = block_sum(a, s_red);
     const double sb = block_sum(b, s_red);
@@ -179,6 +179,128 @@ __global__ void zero_kernel(double* __restrict__ v, int64_t n) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32-arithmetic inner solver of mixed-precision refinement: FP32 vectors and FMAs,
+// scalars (alpha, beta, rho) and the cross-CTA sums of every dot product in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float block_sum_f32(float v, float* smem) {
+    smem[threadIdx.x] = v;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x < 32) {
+        t = smem[threadIdx.x];
+#pragma unroll
+        for (int k = 1; k < kThreads / 32; ++k) t += smem[threadIdx.x + 32 * k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+// FP64 value of an FP32 number, exactly, with integer operations only.
+__device__ __forceinline__ double f32_to_f64(float v) { return widen_f32_bits(__float_as_uint(v)); }
+
+// CTA total in FP32, then the cross-CTA total in FP64 (thread 0 of the last CTA).
+__device__ __forceinline__ bool last_block_total_f32(float v, double* partials, uint32_t* ticket, double* total) {
+    __shared__ float s_f[kThreads];
+    const float cta = block_sum_f32(v, s_f);
+    return last_block_total(threadIdx.x == 0 ? f32_to_f64(cta) : 0.0, partials, ticket, total);
+}
+
+// r = b - q, p = r; rho = r.r, ||b||.
+__global__ void __launch_bounds__(kThreads) cgf_init_kernel(int64_t n, const float* __restrict__ b,
+                                                            const float* __restrict__ q, float* __restrict__ r,
+                                                            float* __restrict__ p, double* __restrict__ partials,
+                                                            CgState* st) {
+    float rr = 0.0f, bb = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const float bi = b[i];
+        const float ri = bi - q[i];
+        r[i] = ri;
+        p[i] = ri;
+        rr = fmaf(ri, ri, rr);
+        bb = fmaf(bi, bi, bb);
+    }
+    __shared__ float s_f[kThreads];
+    const float crr = block_sum_f32(rr, s_f);
+    const float cbb = block_sum_f32(bb, s_f);
+    double trr, tbb;
+    if (last_block_total2(threadIdx.x == 0 ? f32_to_f64(crr) : 0.0, threadIdx.x == 0 ? f32_to_f64(cbb) : 0.0,
+                          partials, &st->ticket, &trr, &tbb) &&
+        threadIdx.x == 0) {
+        st->rho = trr;
+        st->bnorm = sqrt(tbb);
+        st->iters = 0;
+        if (tbb == 0.0 || sqrt(trr) <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* __restrict__ x,
+                                                              float* __restrict__ r, const float* __restrict__ p,
+                                                              const float* __restrict__ q,
+                                                              double* __restrict__ partials, CgState* st) {
+    if (st->done) return;
+    __shared__ float s_alpha;
+    if (threadIdx.x == 0) s_alpha = (float)st->alpha;
+    __syncthreads();
+    const float alpha = s_alpha;
+    float rr = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fmaf(ri, ri, rr);
+    }
+    double tot;
+    if (last_block_total_f32(rr, partials, &st->ticket, &tot) && threadIdx.x == 0) {
+        st->iters += 1;
+        if (sqrt(tot) <= st->tol * st->bnorm) {
+            st->rho = tot;
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        } else {
+            st->beta = tot / st->rho;
+            st->rho = tot;
+            if (st->iters >= st->maxit) {
+                st->done = 1;
+                st->phase = CG_MAXIT;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, const float* __restrict__ r,
+                                                               float* __restrict__ p, const CgState* st) {
+    if (st->done) return;
+    __shared__ float s_beta;
+    if (threadIdx.x == 0) s_beta = (float)st->beta;
+    __syncthreads();
+    const float beta = s_beta;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        p[i] = fmaf(beta, p[i], r[i]);
+}
+
+// Refinement glue: r32 = (float)(r * scale); x += scale64 * (double)d32.
+__global__ void ir_scale_down_kernel(int64_t n, const double* __restrict__ r, double scale,
+                                     float* __restrict__ r32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r32[i] = __double2float_rn(r[i] * scale);
+}
+
+__global__ void ir_correct_kernel(int64_t n, double* __restrict__ x, double scale, const float* __restrict__ d32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fma(scale, f32_to_f64(d32[i]), x[i]);
+}
+
+__global__ void zero_f32_kernel(float* __restrict__ v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static mspv_status ensure_cg_work(mspv_matrix* A) {
@@ -269,13 +391,71 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
     }
 }
 
+static mspv_status ensure_cg_work_f32(mspv_matrix* A) {
+    MSPV_TRY(ensure_cg_work(A));
+    CgWork& w = A->cg;
+    const int64_t n = A->nrows;
+    if (w.rf && w.nf == n) return MSPV_OK;
+    auto f = [](void* p) { if (p) dev_free(p, 0); };
+    f(w.rf); f(w.pf); f(w.qf);
+    w.rf = w.pf = w.qf = nullptr;
+    MSPV_TRY(dev_alloc_n(&w.rf, n));
+    MSPV_TRY(dev_alloc_n(&w.pf, n));
+    MSPV_TRY(dev_alloc_n(&w.qf, n));
+    w.nf = n;
+    return MSPV_OK;
+}
+
+// CG in FP32 arithmetic on A (FP32 or BF16 stored values) for A x32 = b32, x32 from 0.
+// Same iteration and stopping rule as cg_solve; the scalars live in FP64.
+static mspv_status cg_solve_f32(mspv_matrix* A, const float* b32, float* x32, double tol, int32_t maxit,
+                                cudaStream_t s, int32_t* iters) {
+    const int64_t n = A->nrows;
+    *iters = 0;
+    MSPV_TRY(ensure_cg_work_f32(A));
+    CgWork& w = A->cg;
+    CgState* hst = w.host_st;
+    *hst = CgState{};
+    hst->tol = tol;
+    hst->maxit = maxit;
+    MSPV_CUDA_TRY(cudaMemcpyAsync(w.st, hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    const unsigned Gi = (unsigned)wave_grid<cgf_init_kernel>(n);
+    const unsigned Gu = (unsigned)wave_grid<cgf_update_kernel>(n);
+    const unsigned Gp = (unsigned)wave_grid<cgf_pupdate_kernel>(n);
+    MSPV_TRY(launch_spmv_f32(A, x32, w.qf, s, DotEpilogue{nullptr, nullptr}));
+    cgf_init_kernel<<<Gi, kThreads, 0, s>>>(n, b32, w.qf, w.rf, w.pf, w.partials, w.st);
+    MSPV_CUDA_TRY(cudaGetLastError());
+    const DotEpilogue ep{w.st, w.partials};
+    const int every = check_every();
+    int32_t launched = 0;
+    for (;;) {
+        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst->done || launched >= maxit) break;
+        const int32_t batch = std::min<int32_t>(every, maxit - launched);
+        for (int32_t k = 0; k < batch; ++k) {
+            MSPV_TRY(launch_spmv_f32(A, w.pf, w.qf, s, ep));
+            cgf_update_kernel<<<Gu, kThreads, 0, s>>>(n, x32, w.rf, w.pf, w.qf, w.partials, w.st);
+            cgf_pupdate_kernel<<<Gp, kThreads, 0, s>>>(n, w.rf, w.pf, w.st);
+        }
+        MSPV_CUDA_TRY(cudaGetLastError());
+        launched += batch;
+    }
+    *iters = hst->iters;
+    if (hst->phase == CG_BREAKDOWN)
+        return set_error(MSPV_EBREAKDOWN, "cg (fp32 inner): breakdown at iteration %d", hst->iters);
+    return MSPV_OK;
+}
+
 mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, double* x,
                         double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
-                        cudaStream_t s, int32_t* outer_iters, int32_t* inner_iters,
-                        double* relres) {
+                        int32_t inner_fp32, cudaStream_t s, int32_t* outer_iters,
+                        int32_t* inner_iters, double* relres) {
     if (A64->nrows != A64->ncols || Alo->nrows != A64->nrows || Alo->ncols != A64->ncols)
         return set_error(MSPV_EFORMAT, "cg_ir: matrices must be square and of equal size");
     if (max_outer < 0 || maxit_inner < 0) return set_error(MSPV_EINVAL, "cg_ir: negative iteration limit");
+    if (inner_fp32 && Alo->value_type == MSPV_F64)
+        return set_error(MSPV_EFORMAT, "cg_ir: FP32 inner arithmetic needs FP32 or BF16 values in Alo");
     const int64_t n = A64->nrows;
     if (outer_iters) *outer_iters = 0;
     if (inner_iters) *inner_iters = 0;
@@ -283,13 +463,20 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
     if (n == 0) return MSPV_OK;
     MSPV_TRY(ensure_cg_work(A64));
     // outer vectors are separate buffers so that Alo may be the same handle as A64
-    DevBuf rbuf, dbuf, qbuf;
+    DevBuf rbuf, dbuf, qbuf, r32buf, d32buf;
     MSPV_TRY(rbuf.alloc(sizeof(double) * n));
-    MSPV_TRY(dbuf.alloc(sizeof(double) * n));
     MSPV_TRY(qbuf.alloc(sizeof(double) * n));
+    if (inner_fp32) {
+        MSPV_TRY(r32buf.alloc(sizeof(float) * n));
+        MSPV_TRY(d32buf.alloc(sizeof(float) * n));
+    } else {
+        MSPV_TRY(dbuf.alloc(sizeof(double) * n));
+    }
     double* r = rbuf.as<double>();
     double* d = dbuf.as<double>();
     double* q = qbuf.as<double>();
+    float* r32 = r32buf.as<float>();
+    float* d32 = d32buf.as<float>();
     CgState* ost = A64->cg.st + 1;
     CgState* host = A64->cg.host_st + 1;
     *host = CgState{};
@@ -309,21 +496,35 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
             result = MSPV_OK;
             break;
         }
-        const double rel = std::sqrt(host->rho) / host->bnorm;
+        const double rnorm = std::sqrt(host->rho);
+        const double rel = rnorm / host->bnorm;
         if (relres) *relres = rel;
         if (outer_iters) *outer_iters = k;
         if (rel <= tol) { result = MSPV_OK; break; }
         if (k == max_outer) { result = MSPV_ENOTCONV; break; }
-        zero_kernel<<<G, kThreads, 0, s>>>(d, n);
         int32_t it = 0;
-        double inner_rel = 0.0;
-        const mspv_status st = cg_solve(Alo, r, d, inner_tol, maxit_inner, s, &it, &inner_rel);
+        mspv_status st;
+        if (inner_fp32) {
+            // solve A d = r / ||r|| in FP32 (unit right-hand side keeps FP32 in range as the
+            // outer residual shrinks), then x += ||r|| d in FP64
+            ir_scale_down_kernel<<<G, kThreads, 0, s>>>(n, r, 1.0 / rnorm, r32);
+            zero_f32_kernel<<<G, kThreads, 0, s>>>(d32, n);
+            st = cg_solve_f32(Alo, r32, d32, inner_tol, maxit_inner, s, &it);
+            if (st == MSPV_OK) ir_correct_kernel<<<G, kThreads, 0, s>>>(n, x, rnorm, d32);
+        } else {
+            zero_kernel<<<G, kThreads, 0, s>>>(d, n);
+            double inner_rel = 0.0;
+            st = cg_solve(Alo, r, d, inner_tol, maxit_inner, s, &it, &inner_rel);
+            if (st == MSPV_OK || st == MSPV_ENOTCONV) {
+                axpy1_kernel<<<G, kThreads, 0, s>>>(n, x, d);
+                st = MSPV_OK;
+            }
+        }
         total_inner += it;
-        if (st == MSPV_EBREAKDOWN || st == MSPV_ECUDA || st == MSPV_ENOMEM || st == MSPV_EINVAL) {
+        if (st != MSPV_OK) {
             result = st;
             break;
         }
-        axpy1_kernel<<<G, kThreads, 0, s>>>(n, x, d);
         MSPV_CUDA_TRY(cudaGetLastError());
     }
     if (inner_iters) *inner_iters = total_inner;

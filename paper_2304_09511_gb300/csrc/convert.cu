@@ -643,6 +643,7 @@ void free_matrix(mspv_matrix* M) {
     auto f = [](void* p) { if (p) dev_free(p, 0); };
     f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->av); f(M->carry); f(M->row_block);
     f(M->cg.r); f(M->cg.p); f(M->cg.q); f(M->cg.partials); f(M->cg.st);
+    f(M->cg.rf); f(M->cg.pf); f(M->cg.qf);
     if (M->cg.host_st) cudaFreeHost(M->cg.host_st);
     M->ai = M->aj = M->irp = M->doff = nullptr;
     M->av = nullptr;

@@ -156,6 +156,11 @@ struct CgWork {
     int64_t npartials = 0;
     CgState* st = nullptr;
     CgState* host_st = nullptr;   // pinned mirror
+    // FP32 vectors of the FP32-arithmetic inner solver
+    int64_t nf = 0;
+    float* rf = nullptr;
+    float* pf = nullptr;
+    float* qf = nullptr;
 };
 
 // Last CTA of a fused p.q reduction: alpha = rho / p.q, or a breakdown when p.q <= 0
@@ -221,6 +226,10 @@ mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
 // spmv.cu
 mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                         DotEpilogue ep);
+// FP32 arithmetic (FP32/BF16 stored values, FP32 vectors): the inner solver of
+// mixed-precision refinement. EFORMAT for FP64 stored values.
+mspv_status launch_spmv_f32(const mspv_matrix* A, const float* x, float* y, cudaStream_t s,
+                            DotEpilogue ep);
 int64_t spmv_partials_needed(const mspv_matrix* A);   // CTAs of the fused-dot launch
 mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* aj,
                            const double* av, const double* x, double* y, CooCarry* carry,
@@ -233,8 +242,8 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
                      cudaStream_t s, int32_t* iters, double* relres);
 mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, double* x,
                         double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
-                        cudaStream_t s, int32_t* outer_iters, int32_t* inner_iters,
-                        double* relres);
+                        int32_t inner_fp32, cudaStream_t s, int32_t* outer_iters,
+                        int32_t* inner_iters, double* relres);
 
 // block-wide reductions shared by the kernels (defined inline below)
 __device__ __forceinline__ double warp_sum(double v) {
@@ -243,15 +252,19 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the CTA (kThreads threads); the result is valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* smem32) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) smem32[warp] = v;
+// Sum over the CTA (kThreads threads); the result is valid in thread 0. Every value goes
+// through shared memory and warp 0 adds 8 of them per lane before a 5-step shuffle
+// reduction: 13 FP64 warp instructions per CTA instead of 45 for a shuffle reduction in
+// every warp (FP64 issue slots are the scarce resource on GB300). smem holds kThreads
+// doubles. The order is fixed, so the result is deterministic.
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+    smem[threadIdx.x] = v;
     __syncthreads();
     double t = 0.0;
-    if (warp == 0) {
-        t = (lane < (kThreads / 32)) ? smem32[lane] : 0.0;
+    if (threadIdx.x < 32) {
+        t = smem[threadIdx.x];
+#pragma unroll
+        for (int k = 1; k < kThreads / 32; ++k) t += smem[threadIdx.x + 32 * k];
         t = warp_sum(t);
     }
     __syncthreads();
@@ -263,7 +276,7 @@ __device__ __forceinline__ double block_sum(double v, double* smem32) {
 // deterministic. Returns true in exactly one CTA, where thread 0 holds *total.
 __device__ __forceinline__ bool last_block_total(double partial, double* partials,
                                                  uint32_t* ticket, double* total) {
-    __shared__ double s_red[32];
+    __shared__ double s_red[kThreads];
     __shared__ bool s_last;
     double bsum = block_sum(partial, s_red);
     if (threadIdx.x == 0) {

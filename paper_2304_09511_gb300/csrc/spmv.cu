@@ -37,23 +37,20 @@ constexpr int kStageCap = 3072;   // entries staged per CTA (values + gathered x
 constexpr int kLongRun = 128;     // runs longer than this are reduced by the whole CTA
 constexpr int kMaxLongRuns = kStageCap / (kLongRun + 1) + 1;
 constexpr int kRsCap = kStageCap + 4;   // run starts (+1 sentinel), padded so srow stays 16-byte aligned
-constexpr size_t kCsrSmem = 2 * kStageCap * sizeof(double) + kRsCap * sizeof(int32_t);
-constexpr size_t kCooSmem = kCsrSmem + kStageCap * sizeof(int32_t);
 static_assert(kCooWindow <= kStageCap, "COO window must fit the staging buffers");
-static_assert((2 * kStageCap * sizeof(double) + kRsCap * sizeof(int32_t)) % 16 == 0, "srow alignment");
 
 // ---------------------------------------------------------------------------
 // DIA
 // ---------------------------------------------------------------------------
-template <typename VT> struct DiaVec;
-template <> struct DiaVec<double> {
+template <typename VT, typename T> struct DiaVec;
+template <> struct DiaVec<double, double> {
     static constexpr int RPT = 2;
     __device__ __forceinline__ static void load(const double* p, double (&v)[RPT]) {
         const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
         v[0] = t.x; v[1] = t.y;
     }
 };
-template <> struct DiaVec<float> {
+template <> struct DiaVec<float, double> {
     static constexpr int RPT = 4;
     __device__ __forceinline__ static void load(const float* p, double (&v)[RPT]) {
         const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
@@ -61,7 +58,7 @@ template <> struct DiaVec<float> {
         v[2] = widen_f32_bits(t.z); v[3] = widen_f32_bits(t.w);
     }
 };
-template <> struct DiaVec<__nv_bfloat16> {
+template <> struct DiaVec<__nv_bfloat16, double> {
     static constexpr int RPT = 8;
     __device__ __forceinline__ static void load(const __nv_bfloat16* p, double (&v)[RPT]) {
         const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
@@ -73,17 +70,77 @@ template <> struct DiaVec<__nv_bfloat16> {
         }
     }
 };
+template <> struct DiaVec<float, float> {
+    static constexpr int RPT = 4;
+    __device__ __forceinline__ static void load(const float* p, float (&v)[RPT]) {
+        const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <> struct DiaVec<__nv_bfloat16, float> {
+    static constexpr int RPT = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[RPT]) {
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+};
 
 constexpr int kDiaSmemDiags = 256;   // offsets cached in shared memory; more are read from global
 
-// One wave of CTAs, each owning the contiguous rows [blockIdx.x * rows_per_cta, ...):
-// every CTA gets the same work, so no SM idles through a partial last wave.
-template <typename VT>
+// FMA in the arithmetic type (T = double: the FP64 path; T = float: the FP32-arithmetic
+// path of the inner solver of mixed-precision refinement).
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+// Exact FP32 -> FP64 of a per-thread FP32 partial, with integer operations.
+__device__ __forceinline__ double to_f64_exact(double v) { return v; }
+__device__ __forceinline__ double to_f64_exact(float v) { return widen_f32_bits(__float_as_uint(v)); }
+
+// Sum over the CTA in T (thread 0 holds the result); smem holds kThreads values.
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T* smem) {
+    smem[threadIdx.x] = v;
+    __syncthreads();
+    T t = T(0);
+    if (threadIdx.x < 32) {
+        t = smem[threadIdx.x];
+#pragma unroll
+        for (int k = 1; k < kThreads / 32; ++k) t += smem[threadIdx.x + 32 * k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+// Fused dot epilogue: per-thread partials in T are summed over the CTA in T; CTA totals
+// are summed in FP64 by the last CTA, which forms alpha.
+template <typename T>
+__device__ __forceinline__ void finish_dot(T dot, DotEpilogue ep) {
+    double tot;
+    bool last;
+    if constexpr (sizeof(T) == 8) {
+        last = last_block_total(dot, ep.partials, &ep.st->ticket, &tot);
+    } else {
+        __shared__ T s_dot[kThreads];
+        const T cta = block_sum_t(dot, s_dot);
+        last = last_block_total(threadIdx.x == 0 ? to_f64_exact(cta) : 0.0, ep.partials, &ep.st->ticket, &tot);
+    }
+    if (last && threadIdx.x == 0) finish_alpha(ep.st, tot);
+}
+
+// CTA b owns rows [b * rows_per_cta, (b + 1) * rows_per_cta); threads step through them in
+// strips of kThreads * RPT rows.
+template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
-    const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
     int64_t rows_per_cta, DotEpilogue ep) {
-    constexpr int RPT = DiaVec<VT>::RPT;
+    constexpr int RPT = DiaVec<VT, T>::RPT;
     if (ep.st && ep.st->done) return;   // uniform: CG already finished
     __shared__ int32_t s_off[kDiaSmemDiags];
     for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
@@ -91,131 +148,135 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
 
     const int64_t row0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t row1 = (row0 + rows_per_cta < n) ? row0 + rows_per_cta : n;
-    double d = 0.0;
+    T d = T(0);
     for (int64_t i0 = row0 + (int64_t)threadIdx.x * RPT; i0 < row1; i0 += (int64_t)kThreads * RPT) {
-        double acc[RPT];
+        T acc[RPT];
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) acc[r] = 0.0;
+        for (int r = 0; r < RPT; ++r) acc[r] = T(0);
         const VT* col = av + i0;
 #pragma unroll 3
         for (int j = 0; j < ndiags; ++j) {
             const int32_t off = (j < kDiaSmemDiags) ? s_off[j] : __ldg(doff + j);
-            double a[RPT];
-            DiaVec<VT>::load(col + (int64_t)j * npad, a);
+            T a[RPT];
+            DiaVec<VT, T>::load(col + (int64_t)j * npad, a);
             const int64_t k0 = i0 + off;
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
                 const int64_t k = k0 + r;
-                if (k >= 0 && k < n) acc[r] = fma(a[r], __ldg(x + k), acc[r]);
+                if (k >= 0 && k < n) acc[r] = fma_t(a[r], __ldg(x + k), acc[r]);
             }
         }
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             if (i0 + r < n) {
                 y[i0 + r] = acc[r];
-                if (ep.st) d = fma(__ldg(x + i0 + r), acc[r], d);
+                if (ep.st) d = fma_t(__ldg(x + i0 + r), acc[r], d);
             }
         }
     }
-    if (ep.st) {
-        double tot;
-        if (last_block_total(d, ep.partials, &ep.st->ticket, &tot) && threadIdx.x == 0)
-            finish_alpha(ep.st, tot);
-    }
+    if (ep.st) finish_dot(d, ep);
 }
 
 // ---------------------------------------------------------------------------
 // CSR, V lanes per row (long rows)
 // ---------------------------------------------------------------------------
-template <typename VT, int V>
+template <typename T, typename VT>
+__device__ __forceinline__ T convert_value(VT v) {
+    if constexpr (sizeof(T) == 8) return widen(v);
+    else if constexpr (sizeof(VT) == 4) return v;
+    else return __uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);
+}
+
+template <typename VT, typename T, int V>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
-    const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
     DotEpilogue ep) {
     if (ep.st && ep.st->done) return;
     const int64_t gt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int64_t row = gt / V;
     const int lane = threadIdx.x & (V - 1);
-    double sum = 0.0;
+    T sum = T(0);
     if (row < nrows) {
         const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
         for (int32_t j = s + lane; j < e; j += V)
-            sum = fma(widen(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
+            sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
     }
 #pragma unroll
     for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0 && row < nrows) y[row] = sum;
-    if (ep.st) {
-        const double d = (lane == 0 && row < nrows) ? __ldg(x + row) * sum : 0.0;
-        double tot;
-        if (last_block_total(d, ep.partials, &ep.st->ticket, &tot) && threadIdx.x == 0)
-            finish_alpha(ep.st, tot);
-    }
+    if (ep.st) finish_dot((lane == 0 && row < nrows) ? x[row] * sum : T(0), ep);
 }
 
 // ---------------------------------------------------------------------------
-// Staged run-per-thread reduction (CSR and COO)
+// Staged run-per-thread reduction (CSR and COO), generic in the arithmetic type T:
+// T = double is the FP64 path; T = float is the FP32-arithmetic path used by the inner
+// solver of mixed-precision refinement (FP32/BF16 values, FP32 vectors).
 // ---------------------------------------------------------------------------
 // Asynchronous global -> shared copies (LDGSTS). Completion is awaited with
 // cp.async.wait_group, a hardware wait on the issuing thread's own copies.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+template <int N>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    static_assert(N == 4 || N == 8, "copy size");
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    if constexpr (N == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) { cp_async<4>(smem, gmem); }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Value slot k of the staging buffer: FP64 values are staged as is, FP32 values as
-// their 4 raw bytes (widened when read), BF16 values already widened.
-template <typename VT> struct Staged {
-    __device__ __forceinline__ static double get(const double* a_s, int k) { return a_s[k]; }
-};
-template <> struct Staged<float> {
-    __device__ __forceinline__ static double get(const double* a_s, int k) {
+
+// Value slot k of the staging buffer as T. Values of the arithmetic type's size are
+// staged as is; FP32 values on the FP64 path are staged as their 4 raw bytes and widened
+// here; BF16 values are converted while staging.
+template <typename VT, typename T>
+__device__ __forceinline__ T staged_value(const T* a_s, int k) {
+    if constexpr (sizeof(VT) == 4 && sizeof(T) == 8)
         return widen_f32_bits(reinterpret_cast<const uint32_t*>(a_s + k)[0]);
-    }
-};
+    else
+        return a_s[k];
+}
 
 // Stage a window: a_s[k] = av[s+k], x_s[k] = x[aj[s+k]]. Every copy of a phase is in
 // flight at once: first the values and column indices (the index lands in x_s[k]'s
 // slot), then, per thread and for its own slots only, the gathers of x.
-template <typename VT>
+template <typename VT, typename T>
 __device__ __forceinline__ void stage_window(const int32_t* __restrict__ aj,
                                              const VT* __restrict__ av,
-                                             const double* __restrict__ x, int64_t s, int len,
-                                             double* __restrict__ a_s, double* __restrict__ x_s) {
-    int32_t* slot_idx = reinterpret_cast<int32_t*>(x_s);   // aj of entry k at int index 2k
+                                             const T* __restrict__ x, int64_t s, int len,
+                                             T* __restrict__ a_s, T* __restrict__ x_s) {
+    constexpr int STRIDE = sizeof(T) / 4;   // int32 slots per staged entry
+    int32_t* slot_idx = reinterpret_cast<int32_t*>(x_s);
     for (int k = threadIdx.x; k < len; k += kThreads) {
-        if constexpr (sizeof(VT) == 8) cp_async8(a_s + k, av + s + k);
+        if constexpr (sizeof(VT) == sizeof(T)) cp_async<sizeof(T)>(a_s + k, av + s + k);
         else if constexpr (sizeof(VT) == 4) cp_async4(a_s + k, av + s + k);
-        else a_s[k] = widen(__ldcs(av + s + k));
-        cp_async4(slot_idx + 2 * k, aj + s + k);
+        else a_s[k] = convert_value<T>(__ldcs(av + s + k));
+        cp_async4(slot_idx + STRIDE * k, aj + s + k);
     }
     cp_async_wait_all();
-    for (int k = threadIdx.x; k < len; k += kThreads) cp_async8(x_s + k, x + slot_idx[2 * k]);
+    for (int k = threadIdx.x; k < len; k += kThreads) cp_async<sizeof(T)>(x_s + k, x + slot_idx[STRIDE * k]);
     cp_async_wait_all();
 }
 
 // Left-to-right FMA chain over staged entries [b, e).
-template <typename VT>
-__device__ __forceinline__ double run_fma(const double* __restrict__ a_s,
-                                          const double* __restrict__ x_s, int b, int e) {
-    double sum = 0.0;
+template <typename VT, typename T>
+__device__ __forceinline__ T run_fma(const T* __restrict__ a_s, const T* __restrict__ x_s, int b, int e) {
+    T sum = T(0);
     int j = b;
     for (; j + 4 <= e; j += 4) {
-        sum = fma(Staged<VT>::get(a_s, j), x_s[j], sum);
-        sum = fma(Staged<VT>::get(a_s, j + 1), x_s[j + 1], sum);
-        sum = fma(Staged<VT>::get(a_s, j + 2), x_s[j + 2], sum);
-        sum = fma(Staged<VT>::get(a_s, j + 3), x_s[j + 3], sum);
+        sum = fma_t(staged_value<VT>(a_s, j), x_s[j], sum);
+        sum = fma_t(staged_value<VT>(a_s, j + 1), x_s[j + 1], sum);
+        sum = fma_t(staged_value<VT>(a_s, j + 2), x_s[j + 2], sum);
+        sum = fma_t(staged_value<VT>(a_s, j + 3), x_s[j + 3], sum);
     }
-    for (; j < e; ++j) sum = fma(Staged<VT>::get(a_s, j), x_s[j], sum);
+    for (; j < e; ++j) sum = fma_t(staged_value<VT>(a_s, j), x_s[j], sum);
     return sum;
 }
+
 
 // Exclusive scan of one int per thread over the CTA; *total gets the sum.
 __device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
@@ -248,13 +309,12 @@ __device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
 
 // Sum every run [rs[i], rs[i+1]) of the staged window, calling emit(i, sum) once per
 // run: runs up to kLongRun entries in one thread each, longer runs by the whole CTA.
-template <typename VT, typename Emit>
-__device__ __forceinline__ void reduce_runs(const double* __restrict__ a_s,
-                                            const double* __restrict__ x_s,
+template <typename VT, typename T, typename Emit>
+__device__ __forceinline__ void reduce_runs(const T* __restrict__ a_s, const T* __restrict__ x_s,
                                             const int32_t* __restrict__ rs, int nruns, Emit emit) {
     __shared__ int s_long[kMaxLongRuns];
     __shared__ int s_nlong;
-    __shared__ double s_red[32];
+    __shared__ T s_red_t[kThreads];
     if (threadIdx.x == 0) s_nlong = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < nruns; i += kThreads) {
@@ -270,30 +330,35 @@ __device__ __forceinline__ void reduce_runs(const double* __restrict__ a_s,
     for (int l = 0; l < nlong; ++l) {
         const int i = s_long[l];
         const int b = rs[i], e = rs[i + 1];
-        double part = 0.0;
-        for (int j = b + threadIdx.x; j < e; j += kThreads)
-            part = fma(Staged<VT>::get(a_s, j), x_s[j], part);
-        const double sum = block_sum(part, s_red);
+        T part = T(0);
+        for (int j = b + threadIdx.x; j < e; j += kThreads) part = fma_t(staged_value<VT>(a_s, j), x_s[j], part);
+        const T sum = block_sum_t(part, s_red_t);
         if (threadIdx.x == 0) emit(i, sum);
     }
 }
 
+template <typename T>
+constexpr size_t csr_smem() { return 2 * kStageCap * sizeof(T) + kRsCap * sizeof(int32_t); }
+template <typename T>
+constexpr size_t coo_smem() { return csr_smem<T>() + kStageCap * sizeof(int32_t); }
+static_assert(csr_smem<double>() % 16 == 0 && csr_smem<float>() % 16 == 0, "srow alignment");
+
 // CSR: CTA b takes rows [row_block[b], row_block[b+1]), the rows whose first entry lies
 // in entry window b. Blocks too large to stage are reduced row by row by the whole CTA.
-template <typename VT>
+template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
     const int32_t* __restrict__ irp, const int32_t* __restrict__ aj, const VT* __restrict__ av,
-    const int32_t* __restrict__ row_block, const double* __restrict__ x, double* __restrict__ y,
+    const int32_t* __restrict__ row_block, const T* __restrict__ x, T* __restrict__ y,
     DotEpilogue ep) {
     if (ep.st && ep.st->done) return;
-    extern __shared__ __align__(16) double smem[];
-    double* a_s = smem;
-    double* x_s = a_s + kStageCap;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* a_s = reinterpret_cast<T*>(smem_raw);
+    T* x_s = a_s + kStageCap;
     int32_t* rs = reinterpret_cast<int32_t*>(x_s + kStageCap);
-    __shared__ double s_red[32];
+    __shared__ T s_red_t[kThreads];
     const int32_t rb = row_block[blockIdx.x], re = row_block[blockIdx.x + 1];
     const int nr = re - rb;
-    double dot = 0.0;
+    T dot = T(0);
     if (nr > 0) {
         const int32_t s = __ldg(irp + rb), e = __ldg(irp + re);
         const int len = e - s;
@@ -301,33 +366,29 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
             for (int i = threadIdx.x; i <= nr; i += kThreads) rs[i] = __ldg(irp + rb + i) - s;
             stage_window(aj, av, x, s, len, a_s, x_s);
             __syncthreads();
-            reduce_runs<VT>(a_s, x_s, rs, nr, [&](int i, double sum) {
+            reduce_runs<VT>(a_s, x_s, rs, nr, [&](int i, T sum) {
                 y[rb + i] = sum;
-                if (ep.st) dot = fma(__ldg(x + rb + i), sum, dot);
+                if (ep.st) dot = fma_t(x[rb + i], sum, dot);
             });
         } else {
             for (int32_t r = rb; r < re; ++r) {   // uniform over the CTA
                 const int32_t a = __ldg(irp + r), b = __ldg(irp + r + 1);
                 if (a == b) {
-                    if (threadIdx.x == 0) y[r] = 0.0;
+                    if (threadIdx.x == 0) y[r] = T(0);
                     continue;
                 }
-                double part = 0.0;
+                T part = T(0);
                 for (int32_t j = a + threadIdx.x; j < b; j += kThreads)
-                    part = fma(widen(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
-                const double sum = block_sum(part, s_red);
+                    part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
+                const T sum = block_sum_t(part, s_red_t);
                 if (threadIdx.x == 0) {
                     y[r] = sum;
-                    if (ep.st) dot = fma(__ldg(x + r), sum, dot);
+                    if (ep.st) dot = fma_t(x[r], sum, dot);
                 }
             }
         }
     }
-    if (ep.st) {
-        double tot;
-        if (last_block_total(dot, ep.partials, &ep.st->ticket, &tot) && threadIdx.x == 0)
-            finish_alpha(ep.st, tot);
-    }
+    if (ep.st) finish_dot(dot, ep);
 }
 
 // First row of each entry window: row_block[w] = first r in [0, n] with irp[r] >= w*W,
@@ -345,15 +406,15 @@ __global__ void csr_row_block_kernel(const int32_t* __restrict__ irp, int32_t n,
 }
 
 // COO: CTA w takes entries [w*W, (w+1)*W) of the sorted arrays.
-template <typename VT>
+template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
-    const VT* __restrict__ av, const double* __restrict__ x, double* __restrict__ y,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
     CooCarry* __restrict__ carry, const CgState* st) {
     if (st && st->done) return;
-    extern __shared__ __align__(16) double smem[];
-    double* a_s = smem;
-    double* x_s = a_s + kStageCap;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* a_s = reinterpret_cast<T*>(smem_raw);
+    T* x_s = a_s + kStageCap;
     int32_t* rs = reinterpret_cast<int32_t*>(x_s + kStageCap);
     int32_t* srow = rs + kRsCap;
     __shared__ int s_warp[kThreads / 32 + 1];
@@ -403,14 +464,14 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     for (int i = threadIdx.x; i < nruns; i += kThreads) {
         const int32_t r = srow[rs[i]];
         const int32_t prev = (i > 0) ? srow[rs[i] - 1] : row_before;
-        for (int32_t z = prev + 1; z < r; ++z) y[z] = 0.0;
+        for (int32_t z = prev + 1; z < r; ++z) y[z] = T(0);
     }
-    reduce_runs<VT>(a_s, x_s, rs, nruns, [&](int i, double sum) {
+    reduce_runs<VT>(a_s, x_s, rs, nruns, [&](int i, T sum) {
         const int32_t r = srow[rs[i]];
         const bool to_head = (i == 0) && cont_prev;
         const bool to_tail = (i == nruns - 1) && cont_next;
-        if (to_head) carry[w].head = sum;
-        if (to_tail) carry[w].tail = sum;
+        if (to_head) carry[w].head = to_f64_exact(sum);
+        if (to_tail) carry[w].tail = to_f64_exact(sum);
         if (!to_head && !to_tail) y[r] = sum;
     });
     if (threadIdx.x == 0) {
@@ -418,13 +479,14 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
         carry[w].row_last = row_last;
     }
     if (s + len == nnz)   // empty rows after the last entry
-        for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) y[z] = 0.0;
+        for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) y[z] = T(0);
 }
 
 // Rows spanning windows: the window where such a row starts adds its tail, the heads of
 // the windows it covers entirely, and the head of the window where it ends, in order.
+template <typename T>
 __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_t nwin,
-                                      double* __restrict__ y, const CgState* st) {
+                                      T* __restrict__ y, const CgState* st) {
     if (st && st->done) return;
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwin - 1) return;   // the last window cannot continue into another
@@ -443,27 +505,26 @@ __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_
         if (d_single && d_next) ++v;
         else break;
     }
-    y[c.row_last] = sum;
+    y[c.row_last] = (T)sum;
 }
 
-__global__ void fill_zero_kernel(double* __restrict__ y, int64_t n) {
+template <typename T>
+__global__ void fill_zero_kernel(T* __restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = 0.0;
+        y[i] = T(0);
 }
 
 // p.q for the COO path (its SpMV has no single pass to fuse into); last CTA forms alpha.
-__global__ void __launch_bounds__(kThreads) dot_alpha_kernel(int64_t n, const double* __restrict__ p,
-                                                             const double* __restrict__ q,
-                                                             DotEpilogue ep) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dot_alpha_kernel(int64_t n, const T* __restrict__ p,
+                                                             const T* __restrict__ q, DotEpilogue ep) {
     if (ep.st->done) return;
-    double d = 0.0;
+    T d = T(0);
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * kThreads)
-        d = fma(p[i], q[i], d);
-    double tot;
-    if (last_block_total(d, ep.partials, &ep.st->ticket, &tot) && threadIdx.x == 0)
-        finish_alpha(ep.st, tot);
+        d = fma_t(p[i], q[i], d);
+    finish_dot(d, ep);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,37 +567,27 @@ static int64_t vector_grid(int64_t n) {
     return b < 1 ? 1 : b;
 }
 
-// DIA launch shape: G CTAs (at most one wave of resident CTAs), each owning an equal,
-// 8-row-aligned range of rows (8 keeps every 128-bit value load aligned).
-template <typename VT>
-static void dia_shape(int32_t n, int64_t* grid, int64_t* rows_per_cta) {
-    constexpr int RPT = DiaVec<VT>::RPT;
-    static const int per_sm = [] {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, spmv_dia_kernel<VT>, kThreads, 0) != cudaSuccess ||
-            b < 1)
-            b = 4;
-        return b;
+// Raise a kernel's dynamic shared-memory limit once (per kernel instantiation).
+template <auto Kernel>
+static void allow_smem(size_t bytes) {
+    static const bool ok = [bytes] {
+        return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
     }();
-    int64_t g = ((int64_t)n + (int64_t)kThreads * RPT - 1) / ((int64_t)kThreads * RPT);
-    const int64_t wave = (int64_t)kNumSMs * per_sm;
-    if (g > wave) g = wave;
-    if (g < 1) g = 1;
-    int64_t r = ((int64_t)n + g - 1) / g;
-    r = (r + 7) / 8 * 8;
-    *grid = ((int64_t)n + r - 1) / r;
-    if (*grid < 1) *grid = 1;
-    *rows_per_cta = r;
+    (void)ok;
 }
+
+// DIA launch shape: one CTA per strip of kThreads * RPT consecutive rows. Consecutive
+// CTAs run on consecutive strips, so the CTAs in flight read one contiguous stretch of
+// each diagonal and of x (DRAM and L2 friendly). Spreading one wave of CTAs over distant
+// equal row ranges instead balances the tail but measured ~10% slower on GB300.
+static int64_t dia_rpt(int vt) { return vt == MSPV_F64 ? 2 : (vt == MSPV_F32 ? 4 : 8); }
 
 int64_t spmv_partials_needed(const mspv_matrix* A) {
     switch (A->format) {
         case MSPV_DIA: {
-            int64_t grid, rows;
-            if (A->value_type == MSPV_F64) dia_shape<double>(A->nrows, &grid, &rows);
-            else if (A->value_type == MSPV_F32) dia_shape<float>(A->nrows, &grid, &rows);
-            else dia_shape<__nv_bfloat16>(A->nrows, &grid, &rows);
-            return grid;
+            const int64_t strip = (int64_t)kThreads * dia_rpt(A->value_type);
+            const int64_t g = ((int64_t)A->nrows + strip - 1) / strip;
+            return g < 1 ? 1 : g;
         }
         case MSPV_CSR:
             return A->csr_vector == 0 ? A->nblocks : blocks_for((int64_t)A->nrows * A->csr_vector);
@@ -545,35 +596,31 @@ int64_t spmv_partials_needed(const mspv_matrix* A) {
     }
 }
 
-template <typename VT>
-static void launch_dia(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
-                       DotEpilogue ep) {
-    int64_t grid, rows;
-    dia_shape<VT>(A->nrows, &grid, &rows);
-    spmv_dia_kernel<VT><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
-                                                            static_cast<const VT*>(A->av), x, y, rows, ep);
+template <typename VT, typename T>
+static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
+    constexpr int RPT = DiaVec<VT, T>::RPT;
+    const int64_t strip = (int64_t)kThreads * RPT;
+    int64_t grid = ((int64_t)A->nrows + strip - 1) / strip;
+    if (grid < 1) grid = 1;
+    spmv_dia_kernel<VT, T><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
+                                                               static_cast<const VT*>(A->av), x, y, strip, ep);
 }
 
-template <typename VT>
-static void launch_csr(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
-                       DotEpilogue ep) {
+template <typename VT, typename T>
+static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
     const VT* av = static_cast<const VT*>(A->av);
     const int V = A->csr_vector;
     if (V == 0) {
-        static const bool attr = [] {
-            return cudaFuncSetAttribute(spmv_csr_stage_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kCsrSmem) == cudaSuccess;
-        }();
-        (void)attr;
-        spmv_csr_stage_kernel<VT><<<(unsigned)A->nblocks, kThreads, kCsrSmem, s>>>(A->irp, A->aj, av,
-                                                                                   A->row_block, x, y, ep);
+        allow_smem<spmv_csr_stage_kernel<VT, T>>(csr_smem<T>());
+        spmv_csr_stage_kernel<VT, T><<<(unsigned)A->nblocks, kThreads, csr_smem<T>(), s>>>(
+            A->irp, A->aj, av, A->row_block, x, y, ep);
         return;
     }
     const unsigned grid = blocks_for((int64_t)A->nrows * V);
-#define MSPV_CSR_CASE(VV)                                                                 \
-    case VV:                                                                              \
-        spmv_csr_vector_kernel<VT, VV><<<grid, kThreads, 0, s>>>(A->nrows, A->irp, A->aj, \
-                                                                 av, x, y, ep);           \
+#define MSPV_CSR_CASE(VV)                                                                    \
+    case VV:                                                                                 \
+        spmv_csr_vector_kernel<VT, T, VV><<<grid, kThreads, 0, s>>>(A->nrows, A->irp, A->aj, \
+                                                                    av, x, y, ep);           \
         break;
     switch (V) {
         MSPV_CSR_CASE(1)
@@ -587,21 +634,21 @@ static void launch_csr(const mspv_matrix* A, const double* x, double* y, cudaStr
 #undef MSPV_CSR_CASE
 }
 
-template <typename VT>
-static void launch_coo(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
-                       DotEpilogue ep) {
-    const VT* av = static_cast<const VT*>(A->av);
-    static const bool attr = [] {
-        return cudaFuncSetAttribute(spmv_coo_stage_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kCooSmem) == cudaSuccess;
-    }();
-    (void)attr;
-    spmv_coo_stage_kernel<VT><<<(unsigned)A->nchunks, kThreads, kCooSmem, s>>>(
-        A->nrows, A->nnz, A->ai, A->aj, av, x, y, A->carry, ep.st);
-    if (A->nchunks > 1)
-        spmv_coo_fixup_kernel<<<blocks_for(A->nchunks), kThreads, 0, s>>>(A->carry, A->nchunks, y, ep.st);
+template <typename VT, typename T>
+static void launch_coo_windows(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* aj, const VT* av,
+                               const T* x, T* y, CooCarry* carry, int64_t nwin, cudaStream_t s, const CgState* st) {
+    allow_smem<spmv_coo_stage_kernel<VT, T>>(coo_smem<T>());
+    spmv_coo_stage_kernel<VT, T><<<(unsigned)nwin, kThreads, coo_smem<T>(), s>>>(nrows, nnz, ai, aj, av, x, y,
+                                                                                 carry, st);
+    if (nwin > 1) spmv_coo_fixup_kernel<T><<<blocks_for(nwin), kThreads, 0, s>>>(carry, nwin, y, st);
+}
+
+template <typename VT, typename T>
+static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
+    launch_coo_windows<VT, T>(A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry,
+                              A->nchunks, s, ep.st);
     if (ep.st)
-        dot_alpha_kernel<<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(A->nrows, x, y, ep);
+        dot_alpha_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(A->nrows, x, y, ep);
 }
 
 // COO SpMV on raw, row-sorted FP64 device triplets with caller-provided carry records
@@ -611,53 +658,63 @@ mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const 
                            cudaStream_t s) {
     if (nrows == 0) return MSPV_OK;
     if (nnz == 0) {
-        fill_zero_kernel<<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows);
+        fill_zero_kernel<double><<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows);
         MSPV_CUDA_TRY(cudaGetLastError());
         return MSPV_OK;
     }
-    static const bool attr = [] {
-        return cudaFuncSetAttribute(spmv_coo_stage_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kCooSmem) == cudaSuccess;
-    }();
-    (void)attr;
     const int64_t nwin = (nnz + kCooWindow - 1) / kCooWindow;
-    spmv_coo_stage_kernel<double><<<(unsigned)nwin, kThreads, kCooSmem, s>>>(nrows, nnz, ai, aj, av, x, y,
-                                                                            carry, nullptr);
-    if (nwin > 1)
-        spmv_coo_fixup_kernel<<<blocks_for(nwin), kThreads, 0, s>>>(carry, nwin, y, nullptr);
+    launch_coo_windows<double, double>(nrows, nnz, ai, aj, av, x, y, carry, nwin, s, nullptr);
     MSPV_CUDA_TRY(cudaGetLastError());
     return MSPV_OK;
 }
 
-mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
-                        DotEpilogue ep) {
+template <typename T>
+static mspv_status launch_spmv_t(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
     if (A->nrows == 0) return MSPV_OK;
     if (A->format == MSPV_COO && A->nnz == 0) {
         if (ep.st) return set_error(MSPV_EINVAL, "cg: matrix has no entries");
-        fill_zero_kernel<<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, A->nrows);
+        fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, A->nrows);
         MSPV_CUDA_TRY(cudaGetLastError());
         return MSPV_OK;
     }
     const int vt = A->value_type;
+    if constexpr (sizeof(T) == 4) {
+        if (vt == MSPV_F64)
+            return set_error(MSPV_EFORMAT, "FP32 arithmetic needs FP32 or BF16 stored values");
+    }
     switch (A->format) {
         case MSPV_DIA:
-            if (vt == MSPV_F64) launch_dia<double>(A, x, y, s, ep);
-            else if (vt == MSPV_F32) launch_dia<float>(A, x, y, s, ep);
-            else launch_dia<__nv_bfloat16>(A, x, y, s, ep);
+            if constexpr (sizeof(T) == 8) {
+                if (vt == MSPV_F64) { launch_dia<double, T>(A, x, y, s, ep); break; }
+            }
+            if (vt == MSPV_F32) launch_dia<float, T>(A, x, y, s, ep);
+            else launch_dia<__nv_bfloat16, T>(A, x, y, s, ep);
             break;
         case MSPV_CSR:
-            if (vt == MSPV_F64) launch_csr<double>(A, x, y, s, ep);
-            else if (vt == MSPV_F32) launch_csr<float>(A, x, y, s, ep);
-            else launch_csr<__nv_bfloat16>(A, x, y, s, ep);
+            if constexpr (sizeof(T) == 8) {
+                if (vt == MSPV_F64) { launch_csr<double, T>(A, x, y, s, ep); break; }
+            }
+            if (vt == MSPV_F32) launch_csr<float, T>(A, x, y, s, ep);
+            else launch_csr<__nv_bfloat16, T>(A, x, y, s, ep);
             break;
         default:
-            if (vt == MSPV_F64) launch_coo<double>(A, x, y, s, ep);
-            else if (vt == MSPV_F32) launch_coo<float>(A, x, y, s, ep);
-            else launch_coo<__nv_bfloat16>(A, x, y, s, ep);
+            if constexpr (sizeof(T) == 8) {
+                if (vt == MSPV_F64) { launch_coo<double, T>(A, x, y, s, ep); break; }
+            }
+            if (vt == MSPV_F32) launch_coo<float, T>(A, x, y, s, ep);
+            else launch_coo<__nv_bfloat16, T>(A, x, y, s, ep);
             break;
     }
     MSPV_CUDA_TRY(cudaGetLastError());
     return MSPV_OK;
+}
+
+mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s, DotEpilogue ep) {
+    return launch_spmv_t<double>(A, x, y, s, ep);
+}
+
+mspv_status launch_spmv_f32(const mspv_matrix* A, const float* x, float* y, cudaStream_t s, DotEpilogue ep) {
+    return launch_spmv_t<float>(A, x, y, s, ep);
 }
 
 }  // namespace mspv

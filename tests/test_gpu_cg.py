@@ -143,11 +143,13 @@ def test_check_interval_does_not_change_result(mspv, stencil16, monkeypatch):
     assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][1], outs[2][1])
 
 
+@pytest.mark.parametrize("inner_fp32", [False, True], ids=["fp64_inner", "fp32_inner"])
 @pytest.mark.parametrize("vt", ["f32", "bf16"])
-@pytest.mark.parametrize("fmt", ["csr", "dia"])
-def test_iterative_refinement(mspv, orc, vt, fmt):
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_iterative_refinement(mspv, orc, vt, fmt, inner_fp32):
     """Perturbed SPD stencil whose values are not exact in FP32/BF16: the FP64 outer loop
-    still reaches 1e-10 relative residual; the answer matches the oracle's IR."""
+    still reaches 1e-10 relative residual, with the inner CG in FP64 or in FP32
+    arithmetic; the answer matches the oracle's refinement (FP64 inner)."""
     g = 20
     n = g ** 3
     r, c, v = synth.stencil27_perturbed(g, 3)
@@ -158,11 +160,21 @@ def test_iterative_refinement(mspv, orc, vt, fmt):
     Olo = orc.with_values(O, vt)
     assert not np.array_equal(Olo.av, O.av)
     b = orc.spmv(O, np.ones(n))
-    res = A64.cg_ir(Alo, dev(b), tol=1e-10, inner_tol=1e-4)
+    res = A64.cg_ir(Alo, dev(b), tol=1e-10, inner_tol=1e-4, inner_fp32=inner_fp32)
     xo, st, outer, inner, rel = orc.cg_ir(O, Olo, b, tol=1e-10, inner_tol=1e-4)
     assert res.converged and st == orc.OK
     assert res.relres <= 1e-10
     x = res.x.cpu().numpy()
     assert np.linalg.norm(b - orc.spmv(O, x)) / np.linalg.norm(b) <= 1.5e-10
-    assert abs(res.outer_iters - outer) <= 1
+    if not inner_fp32:
+        assert abs(res.outer_iters - outer) <= 1
+    else:
+        assert res.outer_iters <= 6
     assert np.max(np.abs(x - xo)) <= 1e-8
+
+
+def test_fp32_inner_needs_low_precision_values(mspv, stencil16):
+    g, n, A, O = stencil16
+    D = A.convert("dia")
+    with pytest.raises(mspv.MspvError, match="EFORMAT"):
+        D.cg_ir(D, dev(np.ones(n)), inner_fp32=True)
