@@ -226,7 +226,7 @@ mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
 // spmv.cu
 mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,
                         DotEpilogue ep);
-// FP32 arithmetic (FP32/BF16 stored values, FP32 vectors): the inner solver of
+// FP32 arithmetic (FP32/BF16 stored values, FP32 vectors, 16-byte aligned): the inner solver of
 // mixed-precision refinement. EFORMAT for FP64 stored values.
 mspv_status launch_spmv_f32(const mspv_matrix* A, const float* x, float* y, cudaStream_t s,
                             DotEpilogue ep);

@@ -133,26 +133,23 @@ __device__ __forceinline__ void finish_dot(T dot, DotEpilogue ep) {
     if (last && threadIdx.x == 0) finish_alpha(ep.st, tot);
 }
 
-// CTA b owns rows [b * rows_per_cta, (b + 1) * rows_per_cta); threads step through them in
-// strips of kThreads * RPT rows.
+// One thread per RPT consecutive rows, one CTA per strip of kThreads * RPT rows.
 template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
-    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
-    int64_t rows_per_cta, DotEpilogue ep) {
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
     constexpr int RPT = DiaVec<VT, T>::RPT;
     if (ep.st && ep.st->done) return;   // uniform: CG already finished
     __shared__ int32_t s_off[kDiaSmemDiags];
     for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
     __syncthreads();
 
-    const int64_t row0 = (int64_t)blockIdx.x * rows_per_cta;
-    const int64_t row1 = (row0 + rows_per_cta < n) ? row0 + rows_per_cta : n;
-    T d = T(0);
-    for (int64_t i0 = row0 + (int64_t)threadIdx.x * RPT; i0 < row1; i0 += (int64_t)kThreads * RPT) {
-        T acc[RPT];
+    const int64_t i0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * RPT;
+    T acc[RPT];
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) acc[r] = T(0);
+    for (int r = 0; r < RPT; ++r) acc[r] = T(0);
+    T d = T(0);
+    if (i0 < n) {
         const VT* col = av + i0;
 #pragma unroll 3
         for (int j = 0; j < ndiags; ++j) {
@@ -173,6 +170,88 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
                 if (ep.st) d = fma_t(__ldg(x + i0 + r), acc[r], d);
             }
         }
+    }
+    if (ep.st) finish_dot(d, ep);
+}
+
+// FP32-arithmetic DIA (inner solver of mixed-precision refinement; x and y are the
+// library's own 16-byte-aligned FP32 vectors). Memory-bound rather than FP64-bound, so
+// load instructions matter: for each diagonal the RPT values x[i0+off .. i0+off+RPT) are
+// read as NW aligned 128-bit windows starting at i0+off rounded down to a multiple of
+// 4, and picked out by the shift m = off & 3, which is the same for the whole warp.
+template <int M, int RPT, int W>
+__device__ __forceinline__ void dia_f32_fma(const float (&a)[RPT], const float (&w)[W], float (&acc)[RPT]) {
+    static_assert(M + RPT <= W, "window too short for the shift");
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) acc[r] = fmaf(a[r], w[M + r], acc[r]);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
+    int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
+    const VT* __restrict__ av, const float* __restrict__ x, float* __restrict__ y, DotEpilogue ep) {
+    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 values) or 8 (BF16 values)
+    constexpr int NW = RPT / 4 + 1;               // windows covering RPT values at any shift
+    if (ep.st && ep.st->done) return;
+    __shared__ int32_t s_off[kDiaSmemDiags];
+    for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
+    __syncthreads();
+    const int64_t i0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * RPT;
+    float acc[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) acc[r] = 0.0f;
+    if (i0 < n) {
+        const VT* col = av + i0;
+#pragma unroll 2
+        for (int j = 0; j < ndiags; ++j) {
+            const int32_t off = (j < kDiaSmemDiags) ? s_off[j] : __ldg(doff + j);
+            float a[RPT];
+            DiaVec<VT, float>::load(col + (int64_t)j * npad, a);
+            const int64_t k0 = i0 + off;
+            const int m = (int)(k0 & 3);
+            const int64_t base = k0 - m;
+            if (base >= 0 && base + 4 * NW <= n) {
+                float w[4 * NW];
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(x + base) + q);
+                    w[4 * q] = t.x; w[4 * q + 1] = t.y; w[4 * q + 2] = t.z; w[4 * q + 3] = t.w;
+                }
+                switch (m) {   // uniform across the warp
+                    case 0: dia_f32_fma<0>(a, w, acc); break;
+                    case 1: dia_f32_fma<1>(a, w, acc); break;
+                    case 2: dia_f32_fma<2>(a, w, acc); break;
+                    default: dia_f32_fma<3>(a, w, acc); break;
+                }
+            } else {   // a strip touching either end of x
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int64_t k = k0 + r;
+                    if (k >= 0 && k < n) acc[r] = fmaf(a[r], __ldg(x + k), acc[r]);
+                }
+            }
+        }
+    }
+    float d = 0.0f;
+    if (i0 + RPT <= n) {
+#pragma unroll
+        for (int q = 0; q < RPT / 4; ++q) {
+            reinterpret_cast<float4*>(y + i0)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            if (ep.st) {
+                const float4 xv = __ldg(reinterpret_cast<const float4*>(x + i0) + q);
+                d = fmaf(xv.x, acc[4 * q], d);
+                d = fmaf(xv.y, acc[4 * q + 1], d);
+                d = fmaf(xv.z, acc[4 * q + 2], d);
+                d = fmaf(xv.w, acc[4 * q + 3], d);
+            }
+        }
+    } else if (i0 < n) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+            if (i0 + r < n) {
+                y[i0 + r] = acc[r];
+                if (ep.st) d = fmaf(__ldg(x + i0 + r), acc[r], d);
+            }
     }
     if (ep.st) finish_dot(d, ep);
 }
@@ -602,8 +681,13 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     const int64_t strip = (int64_t)kThreads * RPT;
     int64_t grid = ((int64_t)A->nrows + strip - 1) / strip;
     if (grid < 1) grid = 1;
-    spmv_dia_kernel<VT, T><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
-                                                               static_cast<const VT*>(A->av), x, y, strip, ep);
+    if constexpr (sizeof(T) == 4) {
+        spmv_dia_f32_kernel<VT><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
+                                                                    static_cast<const VT*>(A->av), x, y, ep);
+    } else {
+        spmv_dia_kernel<VT, T><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
+                                                                   static_cast<const VT*>(A->av), x, y, ep);
+    }
 }
 
 template <typename VT, typename T>
