@@ -227,7 +227,8 @@ def run_mspv(args, world, rank, local):
 
     # gpu launches of this library inside the timed region
     coo_launches = 1 + (1 if (nnz + 255) // 256 > 1 else 0)
-    launches_per_step = coo_launches + 1 + 1 + (2 + 3 * args.cg_iters)
+    # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update
+    launches_per_step = coo_launches + 1 + 1 + (3 + 5 * args.cg_iters)
 
     # end to end through the public API with host buffers: H2D of x and b, D2H of the
     # three SpMV results and the CG solution, inside the timed region

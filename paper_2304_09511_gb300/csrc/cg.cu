@@ -2,15 +2,19 @@
 // with the preconditioner disabled (Sec. VI), and an FP64 iterative-refinement loop
 // around it for low-precision matrix values (not in the paper).
 //
-// One iteration is three kernels on the caller's stream, none of which waits on
-// the host:
-//   1. q = A p with p.q fused into the SpMV epilogue; the last CTA forms alpha.
-//   2. x += alpha p, r -= alpha q, with r.r fused; the last CTA forms rho', tests
-//      convergence, forms beta and counts the iteration.
-//   3. p = r + beta p.
-// Every scalar lives in a device CgState. Once `done` is set all kernels return
-// at entry, so the host may launch past convergence and polls the state only every
-// MSPV_CG_CHECK_EVERY iterations.
+// One iteration is five kernels on the caller's stream, none of which waits on the
+// host or on another CTA:
+//   1. q = A p; each CTA also writes its partial sum of p.q;
+//   2. (one CTA) p.q = sum of the partials in index order; alpha = rho / p.q, or a
+//      breakdown;
+//   3. x += alpha p, r -= alpha q; each CTA writes its partial of r.r;
+//   4. (one CTA) rho' = r.r; convergence test, iteration count, beta = rho' / rho;
+//   5. p = r + beta p.
+// Every scalar lives in a device CgState. Once `done` is set all kernels return at
+// entry, so the host may launch past convergence and polls the state only every
+// MSPV_CG_CHECK_EVERY iterations. Reductions are deterministic (fixed order) and use
+// no fence or atomic: on GB300 a fused last-CTA reduction (fence + atomic ticket in
+// every CTA) measured +16 us on a 60 us SpMV, more than two extra tiny launches.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -18,6 +22,13 @@
 #include "internal.cuh"
 
 namespace mspv {
+
+static int64_t vec_grid(int64_t n) {   // upper bound of every wave_grid() (partials sizing)
+    int64_t b = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)kNumSMs * 8;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : b;
+}
 
 // Grid of a grid-stride vector kernel: one full wave of resident CTAs (SM count x
 // CTAs per SM at this kernel's register use), fewer when n is small.
@@ -34,154 +45,9 @@ static int64_t wave_grid(int64_t n) {
     return g < 1 ? 1 : g;
 }
 
-static int64_t vec_grid(int64_t n) {   // upper bound of every wave_grid() (partials sizing)
-    int64_t b = (n + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)kNumSMs * 8;
-    if (b > cap) b = cap;
-    return b < 1 ? 1 : b;
-}
+// FP64 value of an FP32 number, exactly, with integer operations only.
+__device__ __forceinline__ double f32_to_f64(float v) { return widen_f32_bits(__float_as_uint(v)); }
 
-// Two fused sums reduced by the last CTA (partials holds 2 per CTA).
-__device__ __forceinline__ bool last_block_total2(double a, double b, double* partials,
-                                                  uint32_t* ticket, double* ta, double* tb) {
-    __shared__ double s_red[kThreads];
-    __shared__ bool s_last;
-    const double sa = block_sum(a, s_red);
-    const double sb = block_sum(b, s_red);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = sa;
-        partials[2 * blockIdx.x + 1] = sb;
-        __threadfence();
-        const uint32_t t = atomicAdd(ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    double acc_a = 0.0, acc_b = 0.0;
-    for (uint32_t k = threadIdx.x; k < gridDim.x; k += kThreads) {
-        acc_a += __ldcg(partials + 2 * k);
-        acc_b += __ldcg(partials + 2 * k + 1);
-    }
-    const double totb = block_sum(acc_b, s_red);
-    const double tota = block_sum(acc_a, s_red);
-    if (threadIdx.x == 0) {
-        *ta = tota;
-        *tb = totb;
-        *ticket = 0u;
-    }
-    return true;
-}
-
-// r = b - q (q = A x0), p = r; rho = r.r and ||b|| reduced; convergence at start.
-__global__ void __launch_bounds__(kThreads) cg_init_kernel(int64_t n, const double* __restrict__ b,
-                                                           const double* __restrict__ q,
-                                                           double* __restrict__ r, double* __restrict__ p,
-                                                           double* __restrict__ partials, CgState* st) {
-    double rr = 0.0, bb = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kThreads) {
-        const double bi = b[i];
-        const double ri = bi - q[i];
-        r[i] = ri;
-        p[i] = ri;
-        rr = fma(ri, ri, rr);
-        bb = fma(bi, bi, bb);
-    }
-    double trr, tbb;
-    if (last_block_total2(rr, bb, partials, &st->ticket, &trr, &tbb) && threadIdx.x == 0) {
-        st->rho = trr;
-        st->bnorm = sqrt(tbb);
-        st->iters = 0;
-        if (tbb == 0.0 || sqrt(trr) <= st->tol * st->bnorm) {
-            st->done = 1;
-            st->phase = CG_CONVERGED;
-        }
-    }
-}
-
-// x += alpha p; r -= alpha q; rho' = r.r; convergence, beta, iteration count.
-__global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* __restrict__ x,
-                                                             double* __restrict__ r,
-                                                             const double* __restrict__ p,
-                                                             const double* __restrict__ q,
-                                                             double* __restrict__ partials, CgState* st) {
-    if (st->done) return;
-    const double alpha = st->alpha;
-    double rr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kThreads) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        rr = fma(ri, ri, rr);
-    }
-    double tot;
-    if (last_block_total(rr, partials, &st->ticket, &tot) && threadIdx.x == 0) {
-        st->iters += 1;
-        if (sqrt(tot) <= st->tol * st->bnorm) {
-            st->rho = tot;
-            st->done = 1;
-            st->phase = CG_CONVERGED;
-        } else {
-            st->beta = tot / st->rho;
-            st->rho = tot;
-            if (st->iters >= st->maxit) {
-                st->done = 1;
-                st->phase = CG_MAXIT;
-            }
-        }
-    }
-}
-
-// p = r + beta p
-__global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
-                                                              double* __restrict__ p,
-                                                              const CgState* st) {
-    if (st->done) return;
-    const double beta = st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kThreads)
-        p[i] = fma(beta, p[i], r[i]);
-}
-
-// Iterative refinement helpers: r = b - q with rho = r.r (and ||b|| on the first call).
-__global__ void __launch_bounds__(kThreads) ir_residual_kernel(int64_t n, const double* __restrict__ b,
-                                                               const double* __restrict__ q,
-                                                               double* __restrict__ r,
-                                                               double* __restrict__ partials, CgState* st) {
-    double rr = 0.0, bb = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kThreads) {
-        const double bi = b[i];
-        const double ri = bi - q[i];
-        r[i] = ri;
-        rr = fma(ri, ri, rr);
-        bb = fma(bi, bi, bb);
-    }
-    double trr, tbb;
-    if (last_block_total2(rr, bb, partials, &st->ticket, &trr, &tbb) && threadIdx.x == 0) {
-        st->rho = trr;
-        st->bnorm = sqrt(tbb);
-    }
-}
-
-__global__ void axpy1_kernel(int64_t n, double* __restrict__ x, const double* __restrict__ d) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += d[i];
-}
-
-__global__ void zero_kernel(double* __restrict__ v, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = 0.0;
-}
-
-// ---------------------------------------------------------------------------
-// FP32-arithmetic inner solver of mixed-precision refinement: FP32 vectors and FMAs,
-// scalars (alpha, beta, rho) and the cross-CTA sums of every dot product in FP64.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ float block_sum_f32(float v, float* smem) {
     smem[threadIdx.x] = v;
     __syncthreads();
@@ -197,21 +63,171 @@ __device__ __forceinline__ float block_sum_f32(float v, float* smem) {
     return t;
 }
 
-// FP64 value of an FP32 number, exactly, with integer operations only.
-__device__ __forceinline__ double f32_to_f64(float v) { return widen_f32_bits(__float_as_uint(v)); }
-
-// CTA total in FP32, then the cross-CTA total in FP64 (thread 0 of the last CTA).
-__device__ __forceinline__ bool last_block_total_f32(float v, double* partials, uint32_t* ticket, double* total) {
-    __shared__ float s_f[kThreads];
-    const float cta = block_sum_f32(v, s_f);
-    return last_block_total(threadIdx.x == 0 ? f32_to_f64(cta) : 0.0, partials, ticket, total);
+// CTA partial of a per-thread value: written by thread 0 to partials[blockIdx.x].
+__device__ __forceinline__ void write_partial(double v, double* partials) {
+    __shared__ double s_red[kThreads];
+    const double t = block_sum(v, s_red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+__device__ __forceinline__ void write_partial_f32(float v, double* partials) {
+    __shared__ float s_red[kThreads];
+    const float t = block_sum_f32(v, s_red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = f32_to_f64(t);
 }
 
-// r = b - q, p = r; rho = r.r, ||b||.
+// Sum of count partials in index order (one CTA; valid in thread 0).
+__device__ __forceinline__ double sum_partials(const double* partials, int64_t count) {
+    __shared__ double s_red[kThreads];
+    double acc = 0.0;
+    for (int64_t b = threadIdx.x; b < count; b += kThreads) acc += partials[b];
+    return block_sum(acc, s_red);
+}
+
+// ---------------------------------------------------------------------------
+// scalar kernels (one CTA)
+// ---------------------------------------------------------------------------
+// rho = r.r, ||b||; converged at the start when r is already small enough (or b = 0).
+__global__ void __launch_bounds__(kThreads) cg_start_kernel(const double* __restrict__ prr,
+                                                            const double* __restrict__ pbb, int64_t count,
+                                                            CgState* st) {
+    const double rr = sum_partials(prr, count);
+    const double bb = sum_partials(pbb, count);
+    if (threadIdx.x == 0) {
+        st->rho = rr;
+        st->bnorm = sqrt(bb);
+        st->iters = 0;
+        if (bb == 0.0 || sqrt(rr) <= st->tol * st->bnorm) {
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        }
+    }
+}
+
+// alpha = rho / p.q, or a breakdown when p.q <= 0 or alpha is not finite.
+__global__ void __launch_bounds__(kThreads) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
+                                                            CgState* st) {
+    if (st->done) return;
+    const double pq = sum_partials(partials, count);
+    if (threadIdx.x == 0) finish_alpha(st, pq);
+}
+
+// rho' = r.r; stop when sqrt(rho') <= tol ||b||; beta = rho' / rho; iteration count.
+__global__ void __launch_bounds__(kThreads) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
+                                                           CgState* st) {
+    if (st->done) return;
+    const double rr = sum_partials(partials, count);
+    if (threadIdx.x == 0) {
+        st->iters += 1;
+        if (sqrt(rr) <= st->tol * st->bnorm) {
+            st->rho = rr;
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        } else {
+            st->beta = rr / st->rho;
+            st->rho = rr;
+            if (st->iters >= st->maxit) {
+                st->done = 1;
+                st->phase = CG_MAXIT;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector kernels
+// ---------------------------------------------------------------------------
+// r = b - q (q = A x0), p = r; partials of r.r and b.b.
+__global__ void __launch_bounds__(kThreads) cg_init_kernel(int64_t n, const double* __restrict__ b,
+                                                           const double* __restrict__ q, double* __restrict__ r,
+                                                           double* __restrict__ p, double* __restrict__ prr,
+                                                           double* __restrict__ pbb) {
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double bi = b[i];
+        const double ri = bi - q[i];
+        r[i] = ri;
+        p[i] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    write_partial(rr, prr);
+    write_partial(bb, pbb);
+}
+
+// x += alpha p; r -= alpha q; partial of r.r.
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* __restrict__ x,
+                                                             double* __restrict__ r, const double* __restrict__ p,
+                                                             const double* __restrict__ q,
+                                                             double* __restrict__ partials, const CgState* st) {
+    if (st->done) return;
+    const double alpha = st->alpha;
+    double rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+    }
+    write_partial(rr, partials);
+}
+
+// p = r + beta p
+__global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
+                                                              double* __restrict__ p, const CgState* st) {
+    if (st->done) return;
+    const double beta = st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+// Iterative refinement: r = b - q; partials of r.r and b.b.
+__global__ void __launch_bounds__(kThreads) ir_residual_kernel(int64_t n, const double* __restrict__ b,
+                                                               const double* __restrict__ q, double* __restrict__ r,
+                                                               double* __restrict__ prr, double* __restrict__ pbb) {
+    double rr = 0.0, bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double bi = b[i];
+        const double ri = bi - q[i];
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+    }
+    write_partial(rr, prr);
+    write_partial(bb, pbb);
+}
+
+// rho = r.r and ||b|| of the refinement's outer residual.
+__global__ void __launch_bounds__(kThreads) ir_norms_kernel(const double* __restrict__ prr,
+                                                            const double* __restrict__ pbb, int64_t count,
+                                                            CgState* st) {
+    const double rr = sum_partials(prr, count);
+    const double bb = sum_partials(pbb, count);
+    if (threadIdx.x == 0) {
+        st->rho = rr;
+        st->bnorm = sqrt(bb);
+    }
+}
+
+__global__ void axpy1_kernel(int64_t n, double* __restrict__ x, const double* __restrict__ d) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+
+__global__ void zero_kernel(double* __restrict__ v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// FP32-arithmetic inner solver of mixed-precision refinement: FP32 vectors and FMAs;
+// alpha, beta, rho and the cross-CTA sums of every dot product in FP64. The FP32
+// vectors are the library's own (16-byte aligned): the bulk is processed with 128-bit
+// accesses, the n % 4 tail element by element.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) cgf_init_kernel(int64_t n, const float* __restrict__ b,
                                                             const float* __restrict__ q, float* __restrict__ r,
-                                                            float* __restrict__ p, double* __restrict__ partials,
-                                                            CgState* st) {
+                                                            float* __restrict__ p, double* __restrict__ prr,
+                                                            double* __restrict__ pbb) {
     float rr = 0.0f, bb = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const float bi = b[i];
@@ -221,29 +237,14 @@ __global__ void __launch_bounds__(kThreads) cgf_init_kernel(int64_t n, const flo
         rr = fmaf(ri, ri, rr);
         bb = fmaf(bi, bi, bb);
     }
-    __shared__ float s_f[kThreads];
-    const float crr = block_sum_f32(rr, s_f);
-    const float cbb = block_sum_f32(bb, s_f);
-    double trr, tbb;
-    if (last_block_total2(threadIdx.x == 0 ? f32_to_f64(crr) : 0.0, threadIdx.x == 0 ? f32_to_f64(cbb) : 0.0,
-                          partials, &st->ticket, &trr, &tbb) &&
-        threadIdx.x == 0) {
-        st->rho = trr;
-        st->bnorm = sqrt(tbb);
-        st->iters = 0;
-        if (tbb == 0.0 || sqrt(trr) <= st->tol * st->bnorm) {
-            st->done = 1;
-            st->phase = CG_CONVERGED;
-        }
-    }
+    write_partial_f32(rr, prr);
+    write_partial_f32(bb, pbb);
 }
 
-// The FP32 vectors are the library's own (16-byte aligned); the bulk is processed with
-// 128-bit accesses, the n % 4 tail element by element.
 __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* __restrict__ x,
                                                               float* __restrict__ r, const float* __restrict__ p,
                                                               const float* __restrict__ q,
-                                                              double* __restrict__ partials, CgState* st) {
+                                                              double* __restrict__ partials, const CgState* st) {
     if (st->done) return;
     __shared__ float s_alpha;
     if (threadIdx.x == 0) s_alpha = (float)st->alpha;
@@ -273,22 +274,7 @@ __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* 
         r[i] = ri;
         rr = fmaf(ri, ri, rr);
     }
-    double tot;
-    if (last_block_total_f32(rr, partials, &st->ticket, &tot) && threadIdx.x == 0) {
-        st->iters += 1;
-        if (sqrt(tot) <= st->tol * st->bnorm) {
-            st->rho = tot;
-            st->done = 1;
-            st->phase = CG_CONVERGED;
-        } else {
-            st->beta = tot / st->rho;
-            st->rho = tot;
-            if (st->iters >= st->maxit) {
-                st->done = 1;
-                st->phase = CG_MAXIT;
-            }
-        }
-    }
+    write_partial_f32(rr, partials);
 }
 
 __global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, const float* __restrict__ r,
@@ -311,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, const 
     for (int64_t i = 4 * n4 + t0; i < n; i += stride) p[i] = fmaf(beta, p[i], r[i]);
 }
 
-// Refinement glue: r32 = (float)(r * scale); x += scale64 * (double)d32.
+// Refinement glue: r32 = (float)(r * scale); x += scale * (double)d32.
 __global__ void ir_scale_down_kernel(int64_t n, const double* __restrict__ r, double scale,
                                      float* __restrict__ r32) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -331,10 +317,16 @@ __global__ void zero_f32_kernel(float* __restrict__ v, int64_t n) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Partials needed: one per CTA of the fused-dot SpMV or of a vector kernel, twice over
+// (two dot products share the buffer in the init and residual kernels).
+static int64_t partials_needed(const mspv_matrix* A) {
+    return 2 * std::max<int64_t>(spmv_partials_needed(A), vec_grid(A->nrows));
+}
+
 static mspv_status ensure_cg_work(mspv_matrix* A) {
     CgWork& w = A->cg;
     const int64_t n = A->nrows;
-    const int64_t need_partials = 2 * std::max<int64_t>(spmv_partials_needed(A), vec_grid(n));
+    const int64_t need_partials = partials_needed(A);
     if (w.r && w.n == n && w.npartials >= need_partials) return MSPV_OK;
     auto f = [](void* p) { if (p) dev_free(p, 0); };
     f(w.r); f(w.p); f(w.q); f(w.partials); f(w.st);
@@ -351,10 +343,55 @@ static mspv_status ensure_cg_work(mspv_matrix* A) {
     return MSPV_OK;
 }
 
+static mspv_status ensure_cg_work_f32(mspv_matrix* A) {
+    MSPV_TRY(ensure_cg_work(A));
+    CgWork& w = A->cg;
+    const int64_t n = A->nrows;
+    if (w.rf && w.nf == n) return MSPV_OK;
+    auto f = [](void* p) { if (p) dev_free(p, 0); };
+    f(w.rf); f(w.pf); f(w.qf);
+    w.rf = w.pf = w.qf = nullptr;
+    MSPV_TRY(dev_alloc_n(&w.rf, n));
+    MSPV_TRY(dev_alloc_n(&w.pf, n));
+    MSPV_TRY(dev_alloc_n(&w.qf, n));
+    w.nf = n;
+    return MSPV_OK;
+}
+
 static int check_every() {
     const char* s = std::getenv("MSPV_CG_CHECK_EVERY");
     const int v = s ? std::atoi(s) : 10;
     return v > 0 ? v : 10;
+}
+
+// The CG iteration loop shared by the FP64 and the FP32-arithmetic solver: V is the
+// vector type, Spmv(x, y, ep) launches the SpMV with its p.q partials.
+template <typename V, typename SpmvFn, typename UpdateK, typename PupdateK>
+static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t maxit, cudaStream_t s,
+                              SpmvFn spmv, UpdateK update, PupdateK pupdate, unsigned Gu, unsigned Gp) {
+    CgWork& w = A->cg;
+    CgState* hst = w.host_st;
+    const int64_t n = A->nrows;
+    const int64_t P = spmv_partials_needed(A);
+    const DotEpilogue ep{w.st, w.partials};
+    const int every = check_every();
+    int32_t launched = 0;
+    for (;;) {
+        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst->done || launched >= maxit) break;
+        const int32_t batch = std::min<int32_t>(every, maxit - launched);
+        for (int32_t k = 0; k < batch; ++k) {
+            MSPV_TRY(spmv(p, q, ep));
+            cg_alpha_kernel<<<1, kThreads, 0, s>>>(w.partials, P, w.st);
+            update<<<Gu, kThreads, 0, s>>>(n, x, r, p, q, w.partials, w.st);
+            cg_beta_kernel<<<1, kThreads, 0, s>>>(w.partials, (int64_t)Gu, w.st);
+            pupdate<<<Gp, kThreads, 0, s>>>(n, r, p, w.st);
+        }
+        MSPV_CUDA_TRY(cudaGetLastError());
+        launched += batch;
+    }
+    return MSPV_OK;
 }
 
 mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,
@@ -374,37 +411,27 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
     hst->tol = tol;
     hst->maxit = maxit;
     MSPV_CUDA_TRY(cudaMemcpyAsync(w.st, hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
-    const unsigned G = (unsigned)vec_grid(n);
     const unsigned Gi = (unsigned)wave_grid<cg_init_kernel>(n);
     const unsigned Gu = (unsigned)wave_grid<cg_update_kernel>(n);
     const unsigned Gp = (unsigned)wave_grid<cg_pupdate_kernel>(n);
+    const int64_t half = w.npartials / 2;
 
     MSPV_TRY(launch_spmv(A, x, w.q, s, DotEpilogue{nullptr, nullptr}));
-    cg_init_kernel<<<Gi, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.st);
+    cg_init_kernel<<<Gi, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.partials + half);
+    cg_start_kernel<<<1, kThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
     if (hst->bnorm == 0.0) {   // b = 0: the solution is 0
-        zero_kernel<<<G, kThreads, 0, s>>>(x, n);
+        zero_kernel<<<(unsigned)vec_grid(n), kThreads, 0, s>>>(x, n);
         MSPV_CUDA_TRY(cudaGetLastError());
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));
         return MSPV_OK;
     }
-    const DotEpilogue ep{w.st, w.partials};
-    const int every = check_every();
-    int32_t launched = 0;
-    while (!hst->done && launched < maxit) {
-        const int32_t batch = std::min<int32_t>(every, maxit - launched);
-        for (int32_t k = 0; k < batch; ++k) {
-            MSPV_TRY(launch_spmv(A, w.p, w.q, s, ep));
-            cg_update_kernel<<<Gu, kThreads, 0, s>>>(n, x, w.r, w.p, w.q, w.partials, w.st);
-            cg_pupdate_kernel<<<Gp, kThreads, 0, s>>>(n, w.r, w.p, w.st);
-        }
-        MSPV_CUDA_TRY(cudaGetLastError());
-        launched += batch;
-        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-    }
+    MSPV_TRY(cg_iterate(
+        A, x, w.r, w.p, w.q, maxit, s,
+        [&](const double* pp, double* qq, DotEpilogue ep) { return launch_spmv(A, pp, qq, s, ep); },
+        cg_update_kernel, cg_pupdate_kernel, Gu, Gp));
     if (iters) *iters = hst->iters;
     if (relres) *relres = std::sqrt(hst->rho) / hst->bnorm;
     switch (hst->phase) {
@@ -417,21 +444,6 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
             return set_error(MSPV_ENOTCONV, "cg: %d iterations, relative residual %g above %g", hst->iters,
                              std::sqrt(hst->rho) / hst->bnorm, tol);
     }
-}
-
-static mspv_status ensure_cg_work_f32(mspv_matrix* A) {
-    MSPV_TRY(ensure_cg_work(A));
-    CgWork& w = A->cg;
-    const int64_t n = A->nrows;
-    if (w.rf && w.nf == n) return MSPV_OK;
-    auto f = [](void* p) { if (p) dev_free(p, 0); };
-    f(w.rf); f(w.pf); f(w.qf);
-    w.rf = w.pf = w.qf = nullptr;
-    MSPV_TRY(dev_alloc_n(&w.rf, n));
-    MSPV_TRY(dev_alloc_n(&w.pf, n));
-    MSPV_TRY(dev_alloc_n(&w.qf, n));
-    w.nf = n;
-    return MSPV_OK;
 }
 
 // CG in FP32 arithmetic on A (FP32 or BF16 stored values) for A x32 = b32, x32 from 0.
@@ -450,25 +462,15 @@ static mspv_status cg_solve_f32(mspv_matrix* A, const float* b32, float* x32, do
     const unsigned Gi = (unsigned)wave_grid<cgf_init_kernel>(n);
     const unsigned Gu = (unsigned)wave_grid<cgf_update_kernel>(n);
     const unsigned Gp = (unsigned)wave_grid<cgf_pupdate_kernel>(n);
+    const int64_t half = w.npartials / 2;
     MSPV_TRY(launch_spmv_f32(A, x32, w.qf, s, DotEpilogue{nullptr, nullptr}));
-    cgf_init_kernel<<<Gi, kThreads, 0, s>>>(n, b32, w.qf, w.rf, w.pf, w.partials, w.st);
+    cgf_init_kernel<<<Gi, kThreads, 0, s>>>(n, b32, w.qf, w.rf, w.pf, w.partials, w.partials + half);
+    cg_start_kernel<<<1, kThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
-    const DotEpilogue ep{w.st, w.partials};
-    const int every = check_every();
-    int32_t launched = 0;
-    for (;;) {
-        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hst->done || launched >= maxit) break;
-        const int32_t batch = std::min<int32_t>(every, maxit - launched);
-        for (int32_t k = 0; k < batch; ++k) {
-            MSPV_TRY(launch_spmv_f32(A, w.pf, w.qf, s, ep));
-            cgf_update_kernel<<<Gu, kThreads, 0, s>>>(n, x32, w.rf, w.pf, w.qf, w.partials, w.st);
-            cgf_pupdate_kernel<<<Gp, kThreads, 0, s>>>(n, w.rf, w.pf, w.st);
-        }
-        MSPV_CUDA_TRY(cudaGetLastError());
-        launched += batch;
-    }
+    MSPV_TRY(cg_iterate(
+        A, x32, w.rf, w.pf, w.qf, maxit, s,
+        [&](const float* pp, float* qq, DotEpilogue ep) { return launch_spmv_f32(A, pp, qq, s, ep); },
+        cgf_update_kernel, cgf_pupdate_kernel, Gu, Gp));
     *iters = hst->iters;
     if (hst->phase == CG_BREAKDOWN)
         return set_error(MSPV_EBREAKDOWN, "cg (fp32 inner): breakdown at iteration %d", hst->iters);
@@ -510,11 +512,13 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
     *host = CgState{};
     MSPV_CUDA_TRY(cudaMemcpyAsync(ost, host, sizeof(CgState), cudaMemcpyHostToDevice, s));
     const unsigned G = (unsigned)vec_grid(n);
+    const int64_t half = A64->cg.npartials / 2;
     int32_t total_inner = 0;
     mspv_status result = MSPV_ENOTCONV;
     for (int32_t k = 0;; ++k) {
         MSPV_TRY(launch_spmv(A64, x, q, s, DotEpilogue{nullptr, nullptr}));
-        ir_residual_kernel<<<G, kThreads, 0, s>>>(n, b, q, r, A64->cg.partials, ost);
+        ir_residual_kernel<<<G, kThreads, 0, s>>>(n, b, q, r, A64->cg.partials, A64->cg.partials + half);
+        ir_norms_kernel<<<1, kThreads, 0, s>>>(A64->cg.partials, A64->cg.partials + half, (int64_t)G, ost);
         MSPV_CUDA_TRY(cudaGetLastError());
         MSPV_CUDA_TRY(cudaMemcpyAsync(host, ost, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));
@@ -533,8 +537,8 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
         int32_t it = 0;
         mspv_status st;
         if (inner_fp32) {
-            // solve A d = r / ||r|| in FP32 (unit right-hand side keeps FP32 in range as the
-            // outer residual shrinks), then x += ||r|| d in FP64
+            // solve A d = r / ||r|| in FP32 (a unit right-hand side keeps FP32 in range as
+            // the outer residual shrinks), then x += ||r|| d in FP64
             ir_scale_down_kernel<<<G, kThreads, 0, s>>>(n, r, 1.0 / rnorm, r32);
             zero_f32_kernel<<<G, kThreads, 0, s>>>(d32, n);
             st = cg_solve_f32(Alo, r32, d32, inner_tol, maxit_inner, s, &it);

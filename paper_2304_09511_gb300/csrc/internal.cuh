@@ -125,9 +125,9 @@ struct CgState {
     uint32_t pad;
 };
 
-// Where an SpMV kernel's optional fused epilogue writes: the dot x.y of its input
-// and output (CG's p.q), reduced across CTAs by the last CTA to finish, which then
-// forms alpha = rho / p.q. st == nullptr disables the epilogue.
+// An SpMV kernel's optional epilogue for CG: each CTA writes its partial of the dot x.y
+// of its input and output (p.q) to partials[blockIdx.x]; kernels return at entry once
+// st->done is set. st == nullptr disables both.
 struct DotEpilogue {
     CgState* st;
     double* partials;   // one per CTA of the launch

@@ -117,20 +117,14 @@ __device__ __forceinline__ T block_sum_t(T v, T* smem) {
     return t;
 }
 
-// Fused dot epilogue: per-thread partials in T are summed over the CTA in T; CTA totals
-// are summed in FP64 by the last CTA, which forms alpha.
+// Dot epilogue (CG's p.q): the CTA sums its threads' partials (in T) and thread 0 writes
+// the CTA total, in FP64, to ep.partials[blockIdx.x]. The cross-CTA sum is a separate
+// one-CTA kernel: no fence or atomic holds the CTA here.
 template <typename T>
 __device__ __forceinline__ void finish_dot(T dot, DotEpilogue ep) {
-    double tot;
-    bool last;
-    if constexpr (sizeof(T) == 8) {
-        last = last_block_total(dot, ep.partials, &ep.st->ticket, &tot);
-    } else {
-        __shared__ T s_dot[kThreads];
-        const T cta = block_sum_t(dot, s_dot);
-        last = last_block_total(threadIdx.x == 0 ? to_f64_exact(cta) : 0.0, ep.partials, &ep.st->ticket, &tot);
-    }
-    if (last && threadIdx.x == 0) finish_alpha(ep.st, tot);
+    __shared__ T s_dot[kThreads];
+    const T cta = block_sum_t(dot, s_dot);
+    if (threadIdx.x == 0) ep.partials[blockIdx.x] = to_f64_exact(cta);
 }
 
 // One thread per RPT consecutive rows, one CTA per strip of kThreads * RPT rows.
