@@ -549,6 +549,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
             }
             MSPV_TRY(exclusive_scan_i32(M->irp, M->irp, M->nrows, M->irp + M->nrows, s));
             M->csr_vector = choose_csr_vector(M->row_mean, M->row_std, M->row_max);
+            M->csr_block = choose_csr_block_kernel();
             MSPV_TRY(build_csr_row_blocks(M, s));
         }
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));

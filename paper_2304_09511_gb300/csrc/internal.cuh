@@ -185,7 +185,8 @@ struct mspv_matrix {
     int32_t nrows = 0, ncols = 0;
     int64_t nnz = 0;
     int32_t ndiags = 0, npad = 0;
-    int32_t csr_vector = 0;   // 0: staged row-block kernel; 1..32: lanes per row
+    int32_t csr_vector = 0;   // 0: staged kernel; 1..32: lanes per row
+    int32_t csr_block = 0;    // staged kernel: 0 = warp-private staging, 1 = CTA row blocks
     int32_t row_max = 0;
     double row_mean = 0.0, row_std = 0.0;
     int64_t empty_rows = 0;
@@ -236,6 +237,7 @@ mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const 
                            cudaStream_t s);
 int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
+int32_t choose_csr_block_kernel();   // MSPV_CSR_KERNEL=block selects CTA row blocks
 
 // cg.cu
 mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,

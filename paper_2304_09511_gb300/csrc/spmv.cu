@@ -28,6 +28,7 @@
 // partials in index order and forms alpha.
 #include <climits>
 #include <cstdlib>
+#include <string>
 
 #include "internal.cuh"
 
@@ -464,6 +465,93 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
     if (ep.st) finish_dot(dot, ep);
 }
 
+// CSR, warp-private staging. Warp w of the grid takes row groups of 32 consecutive rows
+// (grid-stride); lane l owns row 32g + l. The group's entries [irp[32g], irp[32g+32))
+// are staged through the warp's own slice of shared memory in chunks of WCAP entries
+// (values with cp.async, column indices into the x slots, then the x gathers), and each
+// lane adds the FMAs of its row's part of the chunk, left to right. Warps synchronise
+// only with __syncwarp, so one warp's loads overlap another's FMAs, and all 32 lanes
+// work on rows of similar length (FP64 issue slots are spent on full warps). A group
+// holding a row longer than kWarpLongRow is reduced row by row by the whole warp.
+constexpr int kWarpLongRow = 256;
+template <typename T, int WCAP>
+constexpr size_t csr_warp_smem() { return (size_t)(kThreads / 32) * 2 * WCAP * sizeof(T); }
+
+template <typename VT, typename T, int WCAP>
+__global__ void __launch_bounds__(kThreads) spmv_csr_warp_kernel(
+    int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj, const VT* __restrict__ av,
+    const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
+    if (ep.st && ep.st->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* a_s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * WCAP;
+    T* x_s = a_s + WCAP;
+    constexpr int STRIDE = sizeof(T) / 4;
+    int32_t* slot_idx = reinterpret_cast<int32_t*>(x_s);
+    const int64_t ngroups = ((int64_t)nrows + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * (kThreads / 32);
+    T dot = T(0);
+    for (int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp; g < ngroups; g += wstride) {
+        const int64_t r0 = g * 32;
+        const int64_t row = r0 + lane;
+        const bool has_row = row < nrows;
+        const int32_t myb = has_row ? __ldg(irp + row) : 0;
+        const int32_t mye = has_row ? __ldg(irp + row + 1) : 0;
+        const int nr = (int)((nrows - r0 < 32) ? nrows - r0 : 32);
+        const int32_t s = __shfl_sync(0xffffffffu, myb, 0);
+        const int32_t e = __shfl_sync(0xffffffffu, mye, nr - 1);
+        const bool long_row = has_row && (mye - myb > kWarpLongRow);
+        if (__any_sync(0xffffffffu, long_row)) {
+            // whole warp per row: lane-strided FMAs, then a shuffle reduction
+            for (int q = 0; q < nr; ++q) {
+                const int32_t a = __shfl_sync(0xffffffffu, myb, q), b = __shfl_sync(0xffffffffu, mye, q);
+                T part = T(0);
+                for (int32_t j = a + lane; j < b; j += 32)
+                    part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (lane == q) {
+                    y[row] = part;
+                    if (ep.st) dot = fma_t(x[row], part, dot);
+                }
+            }
+            continue;
+        }
+        T sum = T(0);
+        for (int32_t c0 = s; c0 < e; c0 += WCAP) {
+            const int len = (e - c0 < WCAP) ? e - c0 : WCAP;
+            for (int k = lane; k < len; k += 32) {
+                if constexpr (sizeof(VT) == sizeof(T)) cp_async<sizeof(T)>(a_s + k, av + c0 + k);
+                else if constexpr (sizeof(VT) == 4) cp_async4(a_s + k, av + c0 + k);
+                else a_s[k] = convert_value<T>(__ldcs(av + c0 + k));
+                cp_async4(slot_idx + STRIDE * k, aj + c0 + k);
+            }
+            cp_async_wait_all();
+            for (int k = lane; k < len; k += 32) cp_async<sizeof(T)>(x_s + k, x + slot_idx[STRIDE * k]);
+            cp_async_wait_all();
+            __syncwarp();
+            const int b = (myb - c0 > 0) ? myb - c0 : 0;
+            const int en = (mye - c0 < len) ? mye - c0 : len;
+            if (has_row && b < en) {
+                int j = b;
+                for (; j + 4 <= en; j += 4) {
+                    sum = fma_t(staged_value<VT>(a_s, j), x_s[j], sum);
+                    sum = fma_t(staged_value<VT>(a_s, j + 1), x_s[j + 1], sum);
+                    sum = fma_t(staged_value<VT>(a_s, j + 2), x_s[j + 2], sum);
+                    sum = fma_t(staged_value<VT>(a_s, j + 3), x_s[j + 3], sum);
+                }
+                for (; j < en; ++j) sum = fma_t(staged_value<VT>(a_s, j), x_s[j], sum);
+            }
+            __syncwarp();   // the next chunk overwrites the slice
+        }
+        if (has_row) {
+            y[row] = sum;
+            if (ep.st) dot = fma_t(x[row], sum, dot);
+        }
+    }
+    if (ep.st) finish_dot(dot, ep);
+}
+
 // First row of each entry window: row_block[w] = first r in [0, n] with irp[r] >= w*W,
 // for w < nblocks; row_block[nblocks] = n.
 __global__ void csr_row_block_kernel(const int32_t* __restrict__ irp, int32_t n, int64_t nblocks,
@@ -655,6 +743,8 @@ static void allow_smem(size_t bytes) {
 // equal row ranges instead balances the tail but measured ~10% slower on GB300.
 static int64_t dia_rpt(int vt) { return vt == MSPV_F64 ? 2 : (vt == MSPV_F32 ? 4 : 8); }
 
+static int64_t csr_grid_for(const mspv_matrix* A);
+
 int64_t spmv_partials_needed(const mspv_matrix* A) {
     switch (A->format) {
         case MSPV_DIA: {
@@ -663,7 +753,7 @@ int64_t spmv_partials_needed(const mspv_matrix* A) {
             return g < 1 ? 1 : g;
         }
         case MSPV_CSR:
-            return A->csr_vector == 0 ? A->nblocks : blocks_for((int64_t)A->nrows * A->csr_vector);
+            return csr_grid_for(A);
         default:
             return vector_grid(A->nrows);
     }
@@ -684,10 +774,57 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     }
 }
 
+constexpr int kCsrWarpCap = 512;   // entries per warp slice of the warp-staged CSR kernel
+
+// Which staged CSR kernel a new CSR handle uses: warp-private staging (default) or CTA
+// row blocks (MSPV_CSR_KERNEL=block, read when the handle is built).
+int32_t choose_csr_block_kernel() {
+    const char* v = std::getenv("MSPV_CSR_KERNEL");
+    return (v && std::string(v) == "block") ? 1 : 0;
+}
+
+template <typename VT, typename T>
+static int64_t csr_warp_grid(int32_t nrows) {
+    static const int per_sm = [] {
+        int b = 0;
+        allow_smem<spmv_csr_warp_kernel<VT, T, kCsrWarpCap>>(csr_warp_smem<T, kCsrWarpCap>());
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, spmv_csr_warp_kernel<VT, T, kCsrWarpCap>, kThreads,
+                                                          csr_warp_smem<T, kCsrWarpCap>()) != cudaSuccess ||
+            b < 1)
+            b = 2;
+        return b;
+    }();
+    const int64_t groups = ((int64_t)nrows + 31) / 32;
+    int64_t g = (groups + kThreads / 32 - 1) / (kThreads / 32);
+    const int64_t wave = (int64_t)kNumSMs * per_sm;
+    if (g > wave) g = wave;
+    return g < 1 ? 1 : g;
+}
+
+static int64_t csr_grid_for(const mspv_matrix* A) {
+    if (A->csr_vector != 0) return (int64_t)((A->nrows * (int64_t)A->csr_vector + kThreads - 1) / kThreads);
+    if (A->csr_block) return A->nblocks;
+    if (A->value_type == MSPV_F64) return csr_warp_grid<double, double>(A->nrows);
+    // FP32/BF16 values run the FP64-arithmetic or FP32-arithmetic instantiation; both
+    // have one grid size per value type, the larger of the two bounds the partials
+    const int64_t a = (A->value_type == MSPV_F32) ? csr_warp_grid<float, double>(A->nrows)
+                                                  : csr_warp_grid<__nv_bfloat16, double>(A->nrows);
+    const int64_t b = (A->value_type == MSPV_F32) ? csr_warp_grid<float, float>(A->nrows)
+                                                  : csr_warp_grid<__nv_bfloat16, float>(A->nrows);
+    return a > b ? a : b;
+}
+
 template <typename VT, typename T>
 static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
     const VT* av = static_cast<const VT*>(A->av);
     const int V = A->csr_vector;
+    if (V == 0 && !A->csr_block) {
+        allow_smem<spmv_csr_warp_kernel<VT, T, kCsrWarpCap>>(csr_warp_smem<T, kCsrWarpCap>());
+        const int64_t grid = csr_warp_grid<VT, T>(A->nrows);
+        spmv_csr_warp_kernel<VT, T, kCsrWarpCap><<<(unsigned)grid, kThreads, csr_warp_smem<T, kCsrWarpCap>(), s>>>(
+            A->nrows, A->irp, A->aj, av, x, y, ep);
+        return;
+    }
     if (V == 0) {
         allow_smem<spmv_csr_stage_kernel<VT, T>>(csr_smem<T>());
         spmv_csr_stage_kernel<VT, T><<<(unsigned)A->nblocks, kThreads, csr_smem<T>(), s>>>(

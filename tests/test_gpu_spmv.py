@@ -123,8 +123,11 @@ def test_banded_structure_and_spmv(mspv, orc, case, fmt):
     assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), O, x, orc)
 
 
-@pytest.mark.parametrize("vec", [0, 1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("vec", ["0w", "0b", 1, 2, 4, 8, 16, 32])
 def test_csr_every_kernel_choice(mspv, orc, vec, monkeypatch):
+    if isinstance(vec, str):   # staged kernels: warp-private slices or CTA row blocks
+        monkeypatch.setenv("MSPV_CSR_KERNEL", "block" if vec == "0b" else "warp")
+        vec = 0
     monkeypatch.setenv("MSPV_CSR_VEC", str(vec))
     case = (3000, 3000, 60_000, 21, 0.0, 30)
     A, O = build_pair(mspv, orc, case, True)
