@@ -118,6 +118,30 @@ __device__ __forceinline__ T block_sum_t(T v, T* smem) {
     return t;
 }
 
+// Sum over a CTA of NT threads in T (thread 0 holds the result); smem holds NT values.
+template <typename T, int NT>
+__device__ __forceinline__ T block_sum_nt(T v, T* smem) {
+    smem[threadIdx.x] = v;
+    __syncthreads();
+    T t = T(0);
+    if (threadIdx.x < 32) {
+        t = smem[threadIdx.x];
+#pragma unroll
+        for (int k = 1; k < NT / 32; ++k) t += smem[threadIdx.x + 32 * k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void finish_dot_nt(T dot, DotEpilogue ep) {
+    __shared__ T s_dot[NT];
+    const T cta = block_sum_nt<T, NT>(dot, s_dot);
+    if (threadIdx.x == 0) ep.partials[blockIdx.x] = to_f64_exact(cta);
+}
+
 // Dot epilogue (CG's p.q): the CTA sums its threads' partials (in T) and thread 0 writes
 // the CTA total, in FP64, to ep.partials[blockIdx.x]. The cross-CTA sum is a separate
 // one-CTA kernel: no fence or atomic holds the CTA here.
@@ -474,11 +498,11 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
 // work on rows of similar length (FP64 issue slots are spent on full warps). A group
 // holding a row longer than kWarpLongRow is reduced row by row by the whole warp.
 constexpr int kWarpLongRow = 256;
-template <typename T, int WCAP>
-constexpr size_t csr_warp_smem() { return (size_t)(kThreads / 32) * 2 * WCAP * sizeof(T); }
+template <typename T, int WCAP, int NT>
+constexpr size_t csr_warp_smem() { return (size_t)(NT / 32) * 2 * WCAP * sizeof(T); }
 
-template <typename VT, typename T, int WCAP>
-__global__ void __launch_bounds__(kThreads) spmv_csr_warp_kernel(
+template <typename VT, typename T, int WCAP, int NT>
+__global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj, const VT* __restrict__ av,
     const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
     if (ep.st && ep.st->done) return;
@@ -489,9 +513,9 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_warp_kernel(
     constexpr int STRIDE = sizeof(T) / 4;
     int32_t* slot_idx = reinterpret_cast<int32_t*>(x_s);
     const int64_t ngroups = ((int64_t)nrows + 31) / 32;
-    const int64_t wstride = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t wstride = (int64_t)gridDim.x * (NT / 32);
     T dot = T(0);
-    for (int64_t g = (int64_t)blockIdx.x * (kThreads / 32) + warp; g < ngroups; g += wstride) {
+    for (int64_t g = (int64_t)blockIdx.x * (NT / 32) + warp; g < ngroups; g += wstride) {
         const int64_t r0 = g * 32;
         const int64_t row = r0 + lane;
         const bool has_row = row < nrows;
@@ -549,7 +573,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_warp_kernel(
             if (ep.st) dot = fma_t(x[row], sum, dot);
         }
     }
-    if (ep.st) finish_dot(dot, ep);
+    if (ep.st) finish_dot_nt<T, NT>(dot, ep);
 }
 
 // First row of each entry window: row_block[w] = first r in [0, n] with irp[r] >= w*W,
@@ -774,7 +798,12 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     }
 }
 
-constexpr int kCsrWarpCap = 512;   // entries per warp slice of the warp-staged CSR kernel
+// Warp slice: 1024 entries, so a 32-row group of rows up to 32 entries long is staged
+// in one chunk and every lane's row is summed in the same pass (a group split over
+// chunks leaves lanes idle while the warp still issues the longest lane's FMAs).
+// 128-thread CTAs keep three CTAs (12 warps) per SM within shared memory at FP64.
+constexpr int kCsrWarpCap = 1024;
+constexpr int kCsrWarpThreads = 128;
 
 // Which staged CSR kernel a new CSR handle uses: warp-private staging (default) or CTA
 // row blocks (MSPV_CSR_KERNEL=block, read when the handle is built).
@@ -787,15 +816,15 @@ template <typename VT, typename T>
 static int64_t csr_warp_grid(int32_t nrows) {
     static const int per_sm = [] {
         int b = 0;
-        allow_smem<spmv_csr_warp_kernel<VT, T, kCsrWarpCap>>(csr_warp_smem<T, kCsrWarpCap>());
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, spmv_csr_warp_kernel<VT, T, kCsrWarpCap>, kThreads,
-                                                          csr_warp_smem<T, kCsrWarpCap>()) != cudaSuccess ||
-            b < 1)
+        constexpr auto K = spmv_csr_warp_kernel<VT, T, kCsrWarpCap, kCsrWarpThreads>;
+        constexpr size_t smem = csr_warp_smem<T, kCsrWarpCap, kCsrWarpThreads>();
+        allow_smem<K>(smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kCsrWarpThreads, smem) != cudaSuccess || b < 1)
             b = 2;
         return b;
     }();
     const int64_t groups = ((int64_t)nrows + 31) / 32;
-    int64_t g = (groups + kThreads / 32 - 1) / (kThreads / 32);
+    int64_t g = (groups + kCsrWarpThreads / 32 - 1) / (kCsrWarpThreads / 32);
     const int64_t wave = (int64_t)kNumSMs * per_sm;
     if (g > wave) g = wave;
     return g < 1 ? 1 : g;
@@ -819,10 +848,11 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     const VT* av = static_cast<const VT*>(A->av);
     const int V = A->csr_vector;
     if (V == 0 && !A->csr_block) {
-        allow_smem<spmv_csr_warp_kernel<VT, T, kCsrWarpCap>>(csr_warp_smem<T, kCsrWarpCap>());
+        constexpr auto K = spmv_csr_warp_kernel<VT, T, kCsrWarpCap, kCsrWarpThreads>;
+        constexpr size_t smem = csr_warp_smem<T, kCsrWarpCap, kCsrWarpThreads>();
+        allow_smem<K>(smem);
         const int64_t grid = csr_warp_grid<VT, T>(A->nrows);
-        spmv_csr_warp_kernel<VT, T, kCsrWarpCap><<<(unsigned)grid, kThreads, csr_warp_smem<T, kCsrWarpCap>(), s>>>(
-            A->nrows, A->irp, A->aj, av, x, y, ep);
+        K<<<(unsigned)grid, kCsrWarpThreads, smem, s>>>(A->nrows, A->irp, A->aj, av, x, y, ep);
         return;
     }
     if (V == 0) {
