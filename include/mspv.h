@@ -70,7 +70,7 @@ typedef struct {
     int64_t nnz;             /* stored entries (COO/CSR); for DIA the entries it was built from */
     int32_t ndiags;          /* DIA: number of stored diagonals, else 0 */
     int32_t npad;            /* DIA: padded row count of each diagonal (multiple of 32), else 0 */
-    int32_t csr_vector;      /* CSR: 0 = staged row-block kernel, else lanes per row (1..32) */
+    int32_t csr_vector;      /* CSR: lanes per row (1..32), or 0 for the staged kernels */
     int32_t row_max;         /* longest row */
     double row_mean;         /* mean row length */
     double row_std;          /* standard deviation of row lengths */
@@ -210,11 +210,12 @@ MSPV_API const char* mspv_status_string(mspv_status s);
 
 /*
  * CSR SpMV kernel choice for the given row-length statistics (host only, no device
- * access). 0 selects the staged row-block kernel: a CTA per window of 2048 entries
- * stages the products of the rows starting in it through shared memory and sums
- * each row in Algorithm 2's order (used while the mean row length is at most 256).
- * 32 selects a warp per row (longer rows). MSPV_CSR_VEC (0, 1, 2, 4, 8, 16 or 32)
- * overrides the choice; 1..16 select V lanes per row. Exposed for tests and tuning.
+ * access): V lanes per row, 4 while the mean row length is at most 48, then 8 (<= 96),
+ * 16 (<= 192), 32 (warp per row). Rows longer than 32 V entries are listed when the CSR
+ * handle is built and reduced by one CTA each. MSPV_CSR_VEC (1, 2, 4, 8, 16, 32) overrides
+ * V; MSPV_CSR_VEC=0 selects the staged kernels (values and gathered x staged in shared
+ * memory, one row per thread; MSPV_CSR_KERNEL=block for CTA row blocks instead of warp
+ * slices). Exposed for tests and tuning.
  */
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max);
 

@@ -550,6 +550,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
             MSPV_TRY(exclusive_scan_i32(M->irp, M->irp, M->nrows, M->irp + M->nrows, s));
             M->csr_vector = choose_csr_vector(M->row_mean, M->row_std, M->row_max);
             M->csr_block = choose_csr_block_kernel();
+            if (M->csr_vector > 0) MSPV_TRY(build_csr_long_rows(M, s));
             MSPV_TRY(build_csr_row_blocks(M, s));
         }
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));
@@ -642,7 +643,7 @@ mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, do
 
 void free_matrix(mspv_matrix* M) {
     auto f = [](void* p) { if (p) dev_free(p, 0); };
-    f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->av); f(M->carry); f(M->row_block);
+    f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->av); f(M->carry); f(M->row_block); f(M->long_rows);
     f(M->cg.r); f(M->cg.p); f(M->cg.q); f(M->cg.partials); f(M->cg.st);
     f(M->cg.rf); f(M->cg.pf); f(M->cg.qf);
     if (M->cg.host_st) cudaFreeHost(M->cg.host_st);
@@ -650,6 +651,7 @@ void free_matrix(mspv_matrix* M) {
     M->av = nullptr;
     M->carry = nullptr;
     M->row_block = nullptr;
+    M->long_rows = nullptr;
     M->cg = CgWork{};
 }
 

@@ -202,6 +202,8 @@ struct mspv_matrix {
     mspv::CooCarry* carry = nullptr;   // COO: per-window carries
     int64_t nchunks = 0;               // COO windows
     int32_t* row_block = nullptr;      // CSR: first row of each window, nblocks + 1 entries
+    int32_t* long_rows = nullptr;      // CSR vector kernel: rows longer than 32 * csr_vector
+    int64_t nlong = 0;
     int64_t nblocks = 0;               // CSR windows
 
     mspv::CgWork cg;
@@ -237,6 +239,7 @@ mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const 
                            cudaStream_t s);
 int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
+mspv_status build_csr_long_rows(mspv_matrix* M, cudaStream_t s);
 int32_t choose_csr_block_kernel();   // MSPV_CSR_KERNEL=block selects CTA row blocks
 
 // cg.cu

@@ -285,25 +285,65 @@ __device__ __forceinline__ T convert_value(VT v) {
     else return __uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);
 }
 
+// V lanes per row, lane-strided FMAs and a log2(V)-step shuffle reduction. V = 4 suits
+// short rows on GB300: a warp instruction still covers 8 rows x 32-byte segments
+// (coalesced enough), while the reduction costs 2 FP64 shuffle-adds per 8 rows. Rows
+// longer than long_len are skipped here and reduced by spmv_csr_long_kernel.
 template <typename VT, typename T, int V>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
-    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, int32_t long_len,
     DotEpilogue ep) {
     if (ep.st && ep.st->done) return;
     const int64_t gt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int64_t row = gt / V;
     const int lane = threadIdx.x & (V - 1);
     T sum = T(0);
-    if (row < nrows) {
+    bool mine = row < nrows;
+    if (mine) {
         const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
-        for (int32_t j = s + lane; j < e; j += V)
-            sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
+        if (e - s > long_len) {
+            mine = false;   // written by the long-row kernel
+        } else {
+            for (int32_t j = s + lane; j < e; j += V)
+                sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
+        }
     }
 #pragma unroll
     for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0 && row < nrows) y[row] = sum;
-    if (ep.st) finish_dot((lane == 0 && row < nrows) ? x[row] * sum : T(0), ep);
+    if (lane == 0 && mine) y[row] = sum;
+    if (ep.st) finish_dot((lane == 0 && mine) ? x[row] * sum : T(0), ep);
+}
+
+// One CTA per long row (listed at conversion): strided FMAs, then a CTA reduction.
+template <typename VT, typename T>
+__global__ void __launch_bounds__(kThreads) spmv_csr_long_kernel(
+    const int32_t* __restrict__ long_rows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
+    if (ep.st && ep.st->done) return;
+    __shared__ T s_red[kThreads];
+    const int32_t row = long_rows[blockIdx.x];
+    const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
+    T part = T(0);
+    for (int32_t j = s + threadIdx.x; j < e; j += kThreads)
+        part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
+    const T sum = block_sum_t(part, s_red);
+    if (threadIdx.x == 0) {
+        y[row] = sum;
+        if (ep.st) ep.partials[blockIdx.x] = to_f64_exact(x[row] * sum);
+    }
+}
+
+// Rows longer than long_len, listed in order: flag, scan, compact.
+__global__ void csr_long_flag_kernel(const int32_t* __restrict__ irp, int32_t n, int32_t long_len,
+                                     int32_t* __restrict__ flags) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        flags[r] = (irp[r + 1] - irp[r] > long_len) ? 1 : 0;
+}
+__global__ void csr_long_compact_kernel(const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
+                                        int32_t n, int32_t* __restrict__ out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        if (flags[r]) out[pos[r]] = (int32_t)r;
 }
 
 // ---------------------------------------------------------------------------
@@ -722,10 +762,41 @@ int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen) {
         int v = std::atoi(s);
         if (v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) return v;
     }
-    // staged row blocks while rows are short enough for many of them to share a
-    // window; a warp per row once rows average more than a window's worth per warp
-    if (mean <= 256.0) return 0;
+    // V lanes per row: 4 for short rows (coalesced 32-byte segments, two FP64
+    // shuffle-adds per 8 rows), wider as rows grow; rows longer than 32 V entries are
+    // reduced by a CTA each. The staged kernels (0) are selected only explicitly.
+    if (mean <= 48.0) return 4;
+    if (mean <= 96.0) return 8;
+    if (mean <= 192.0) return 16;
     return 32;
+}
+
+mspv_status build_csr_long_rows(mspv_matrix* M, cudaStream_t s) {
+    M->nlong = 0;
+    if (M->nrows == 0) return MSPV_OK;
+    const int32_t long_len = 32 * M->csr_vector;
+    if (M->row_max <= long_len) return MSPV_OK;
+    DevBuf flags, pos, total;
+    MSPV_TRY(flags.alloc(sizeof(int32_t) * (size_t)M->nrows));
+    MSPV_TRY(pos.alloc(sizeof(int32_t) * (size_t)M->nrows));
+    MSPV_TRY(total.alloc(sizeof(int32_t)));
+    unsigned grid = (unsigned)(((int64_t)M->nrows + kThreads - 1) / kThreads);
+    if (grid > (unsigned)kNumSMs * 64) grid = kNumSMs * 64;
+    csr_long_flag_kernel<<<grid, kThreads, 0, s>>>(M->irp, M->nrows, long_len, flags.as<int32_t>());
+    MSPV_CUDA_TRY(cudaGetLastError());
+    MSPV_TRY(exclusive_scan_i32(flags.as<int32_t>(), pos.as<int32_t>(), M->nrows, total.as<int32_t>(), s));
+    int32_t nl = 0;
+    MSPV_CUDA_TRY(cudaMemcpyAsync(&nl, total.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (nl == 0) return MSPV_OK;
+    MSPV_TRY(dev_alloc_n(&M->long_rows, nl));
+    M->bytes += (int64_t)nl * 4;
+    csr_long_compact_kernel<<<grid, kThreads, 0, s>>>(flags.as<int32_t>(), pos.as<int32_t>(), M->nrows,
+                                                      M->long_rows);
+    MSPV_CUDA_TRY(cudaGetLastError());
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    M->nlong = nl;
+    return MSPV_OK;
 }
 
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s) {
@@ -831,7 +902,8 @@ static int64_t csr_warp_grid(int32_t nrows) {
 }
 
 static int64_t csr_grid_for(const mspv_matrix* A) {
-    if (A->csr_vector != 0) return (int64_t)((A->nrows * (int64_t)A->csr_vector + kThreads - 1) / kThreads);
+    if (A->csr_vector != 0)
+        return (int64_t)((A->nrows * (int64_t)A->csr_vector + kThreads - 1) / kThreads) + A->nlong;
     if (A->csr_block) return A->nblocks;
     if (A->value_type == MSPV_F64) return csr_warp_grid<double, double>(A->nrows);
     // FP32/BF16 values run the FP64-arithmetic or FP32-arithmetic instantiation; both
@@ -862,10 +934,11 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         return;
     }
     const unsigned grid = blocks_for((int64_t)A->nrows * V);
+    const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
 #define MSPV_CSR_CASE(VV)                                                                    \
     case VV:                                                                                 \
         spmv_csr_vector_kernel<VT, T, VV><<<grid, kThreads, 0, s>>>(A->nrows, A->irp, A->aj, \
-                                                                    av, x, y, ep);           \
+                                                                    av, x, y, long_len, ep); \
         break;
     switch (V) {
         MSPV_CSR_CASE(1)
@@ -877,6 +950,11 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         MSPV_CSR_CASE(32)
     }
 #undef MSPV_CSR_CASE
+    if (A->nlong > 0) {
+        const DotEpilogue lep{ep.st, ep.partials ? ep.partials + grid : nullptr};
+        spmv_csr_long_kernel<VT, T><<<(unsigned)A->nlong, kThreads, 0, s>>>(A->long_rows, A->irp, A->aj, av, x, y,
+                                                                            lep);
+    }
 }
 
 template <typename VT, typename T>

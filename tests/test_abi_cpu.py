@@ -47,8 +47,8 @@ def test_status_strings(lib):
     assert lib.mspv_version() >= 100
 
 
-@pytest.mark.parametrize("mean,expect", [(0.0, 0), (1.0, 0), (27.0, 0), (256.0, 0), (256.5, 32),
-                                         (20000.0, 32)])
+@pytest.mark.parametrize("mean,expect", [(0.0, 4), (1.0, 4), (27.0, 4), (48.0, 4), (60.0, 8), (96.0, 8),
+                                         (150.0, 16), (192.5, 32), (20000.0, 32)])
 def test_csr_vector_width_heuristic(lib, mean, expect, monkeypatch):
     monkeypatch.delenv("MSPV_CSR_VEC", raising=False)
     assert lib.mspv_csr_vector_width(mean, 0.0, 0) == expect
@@ -60,7 +60,7 @@ def test_csr_vector_width_override(lib, monkeypatch):
     monkeypatch.setenv("MSPV_CSR_VEC", "0")
     assert lib.mspv_csr_vector_width(900.0, 0.0, 900) == 0
     monkeypatch.setenv("MSPV_CSR_VEC", "7")   # not a power of two: ignored
-    assert lib.mspv_csr_vector_width(27.0, 0.0, 27) == 0
+    assert lib.mspv_csr_vector_width(27.0, 0.0, 27) == 4
 
 
 def _create(lib, nrows, ncols, rows, cols, vals, nnz=None):

@@ -161,6 +161,23 @@ def test_window_edges_of_staged_kernels(mspv, orc):
         assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), orc.convert(O, fmt), x, orc)
 
 
+def test_csr_long_rows_split_off(mspv, orc):
+    """Power-law-like rows: most short, some far above 32 V entries; the long ones are
+    listed at conversion and reduced by a CTA each (also inside CG's fused dot)."""
+    rng = np.random.default_rng(21)
+    n = 20000
+    lens = np.minimum((rng.pareto(1.1, n) * 4 + 1).astype(np.int64), 5000)
+    r = np.repeat(np.arange(n), lens).astype(np.int32)
+    c = rng.integers(0, n, r.size).astype(np.int32)
+    v = rng.uniform(-1, 1, r.size)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    C = A.convert("csr")
+    assert C.info["csr_vector"] == 4 and C.info["row_max"] > 128
+    O = orc.coo_to_csr(orc.canonicalize(n, n, r, c, v))
+    x = synth.uniform_x(n, 3) * 2 - 1
+    assert_spmv_parity(C.spmv(dev(x)).cpu().numpy(), O, x, orc)
+
+
 def test_long_rows_and_chunk_spanning(mspv, orc):
     """A 20,000-entry row spans ~80 COO chunks; short rows around it; empty rows at both ends."""
     rng = np.random.default_rng(3)
