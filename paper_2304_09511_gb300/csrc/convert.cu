@@ -606,7 +606,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
 
 mspv_status ensure_coo_carry(mspv_matrix* M) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
-    M->nchunks = (M->nnz + kCooWindow - 1) / kCooWindow;
+    M->nchunks = (M->nnz + kCooVecChunk - 1) / kCooVecChunk;
     MSPV_TRY(dev_alloc_n(&M->carry, M->nchunks > 0 ? M->nchunks : 1));
     M->bytes += (M->nchunks > 0 ? M->nchunks : 1) * (int64_t)sizeof(CooCarry);
     return MSPV_OK;

@@ -143,7 +143,8 @@ struct CooCarry {
 
 // Entries per CTA window of the staged COO and CSR kernels: values and gathered x are
 // staged in shared memory (16 B per entry, plus 4 B of row index for COO).
-constexpr int kCooWindow = 3072;
+constexpr int kCooWindow = 3072;    // staged COO kernel (allocation-free entry point)
+constexpr int kCooVecChunk = 256;   // run-vector COO kernel: entries per warp
 constexpr int kCsrWindow = 2560;     // a CTA takes the rows that start in its window
 
 // CG workspace, owned by a handle and grown on demand.
@@ -200,7 +201,7 @@ struct mspv_matrix {
     int64_t av_count = 0;
 
     mspv::CooCarry* carry = nullptr;   // COO: per-window carries
-    int64_t nchunks = 0;               // COO windows
+    int64_t nchunks = 0;               // COO chunks of kCooVecChunk entries
     int32_t* row_block = nullptr;      // CSR: first row of each window, nblocks + 1 entries
     int32_t* long_rows = nullptr;      // CSR vector kernel: rows longer than 32 * csr_vector
     int64_t nlong = 0;

@@ -707,6 +707,92 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
         for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) y[z] = T(0);
 }
 
+// COO, run-vector kernel. Warp c takes the chunk of kCooVecChunk sorted entries
+// [c*C, (c+1)*C). Pass 1 (integer only): lanes read the row indices (coalesced), mark
+// where the row changes, and compact the run starts with ballots into the warp's slice
+// of shared memory, zeroing the rows skipped between runs. Pass 2: groups of 4 lanes
+// take one run each, lane-strided FMAs over its entries, then 2 shuffle-adds -- the CSR
+// V = 4 pattern, which on GB300 balances coalescing against FP64 issue slots. Runs cut
+// by a chunk edge leave partial sums in the carry record, added by the fix-up pass.
+constexpr int kCooVecPer = kCooVecChunk / 32;
+
+template <typename VT, typename T>
+__global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
+    int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
+    int64_t nchunks, const CgState* st) {
+    if (st && st->done) return;
+    __shared__ int32_t s_rs[kThreads / 32][kCooVecChunk + 1];
+    __shared__ int32_t s_row[kThreads / 32][kCooVecChunk];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + w;
+    if (c >= nchunks) return;   // whole warp
+    const int64_t c0 = c * kCooVecChunk;
+    const int len = (int)((nnz - c0 < kCooVecChunk) ? nnz - c0 : kCooVecChunk);
+    const int32_t row_before = (c0 > 0) ? __ldg(ai + c0 - 1) : -1;
+    const int32_t row_after = (c0 + len < nnz) ? __ldg(ai + c0 + len) : INT_MAX;
+    int32_t* rs = s_rs[w];
+    int32_t* rrow = s_row[w];
+
+    int32_t rv[kCooVecPer];
+#pragma unroll
+    for (int q = 0; q < kCooVecPer; ++q) {
+        const int k = q * 32 + lane;
+        rv[q] = (k < len) ? __ldcs(ai + c0 + k) : INT_MAX;
+    }
+    int nr = 0;
+    int32_t carry_row = row_before;
+#pragma unroll
+    for (int q = 0; q < kCooVecPer; ++q) {
+        const int k = q * 32 + lane;
+        const int32_t r = rv[q];
+        int32_t prev = __shfl_up_sync(FULL, r, 1);
+        if (lane == 0) prev = carry_row;
+        const bool start = (k < len) && (k == 0 || r != prev);
+        const unsigned ballot = __ballot_sync(FULL, start);
+        if (start) {
+            const int pos = nr + __popc(ballot & ((1u << lane) - 1u));
+            rs[pos] = k;
+            rrow[pos] = r;
+            if (r != prev)
+                for (int32_t z = prev + 1; z < r; ++z) y[z] = T(0);   // empty rows in between
+        }
+        nr += __popc(ballot);
+        carry_row = __shfl_sync(FULL, r, 31);
+    }
+    if (lane == 0) rs[nr] = len;
+    __syncwarp();
+
+    const bool cont_prev = (row_before == rrow[0]);
+    const bool cont_next = (row_after == rrow[nr - 1]);
+    const int grp = lane >> 2, sub = lane & 3;
+    for (int i0 = 0; i0 < nr; i0 += 8) {
+        const int i = i0 + grp;
+        T sum = T(0);
+        if (i < nr) {
+            const int b = rs[i], e = rs[i + 1];
+            for (int j = b + sub; j < e; j += 4)
+                sum = fma_t(convert_value<T>(__ldcs(av + c0 + j)), __ldg(x + __ldcs(aj + c0 + j)), sum);
+        }
+        sum += __shfl_xor_sync(FULL, sum, 1);
+        sum += __shfl_xor_sync(FULL, sum, 2);
+        if (sub == 0 && i < nr) {
+            const bool to_head = (i == 0) && cont_prev;
+            const bool to_tail = (i == nr - 1) && cont_next;
+            if (to_head) carry[c].head = to_f64_exact(sum);
+            if (to_tail) carry[c].tail = to_f64_exact(sum);
+            if (!to_head && !to_tail) y[rrow[i]] = sum;
+        }
+    }
+    if (lane == 0) {
+        carry[c].row_first = rrow[0];
+        carry[c].row_last = rrow[nr - 1];
+    }
+    if (c0 + len == nnz)   // empty rows after the last entry
+        for (int32_t z = rrow[nr - 1] + 1 + lane; z < nrows; z += 32) y[z] = T(0);
+}
+
 // Rows spanning windows: the window where such a row starts adds its tail, the heads of
 // the windows it covers entirely, and the head of the window where it ends, in order.
 template <typename T>
@@ -968,8 +1054,10 @@ static void launch_coo_windows(int32_t nrows, int64_t nnz, const int32_t* ai, co
 
 template <typename VT, typename T>
 static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
-    launch_coo_windows<VT, T>(A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry,
-                              A->nchunks, s, ep.st);
+    const int64_t nch = A->nchunks;
+    spmv_coo_vec_kernel<VT, T><<<(unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(
+        A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, ep.st);
+    if (nch > 1) spmv_coo_fixup_kernel<T><<<blocks_for(nch), kThreads, 0, s>>>(A->carry, nch, y, ep.st);
     if (ep.st)
         dot_alpha_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(A->nrows, x, y, ep);
 }
