@@ -144,7 +144,7 @@ struct CooCarry {
 // Entries per CTA window of the staged COO and CSR kernels: values and gathered x are
 // staged in shared memory (16 B per entry, plus 4 B of row index for COO).
 constexpr int kCooWindow = 3072;    // staged COO kernel (allocation-free entry point)
-constexpr int kCooVecChunk = 256;   // run-vector COO kernel: entries per warp
+constexpr int kCooVecChunk = 1024;  // run-vector COO kernel: entries per warp
 constexpr int kCsrWindow = 2560;     // a CTA takes the rows that start in its window
 
 // CG workspace, owned by a handle and grown on demand.
