@@ -330,6 +330,159 @@ def run_mspv(args, world, rank, local):
 
 
 # ---------------------------------------------------------------------------
+# format selection: run-first tuner labels, MLP selector, held-out regret
+# ---------------------------------------------------------------------------
+SELECTOR_METRIC = "format-selector regret on held-out matrices vs the run-first tuner"
+
+
+def _regret(ms: np.ndarray, picks: np.ndarray) -> dict:
+    best = ms.min(axis=1)
+    chosen = ms[np.arange(len(picks)), picks]
+    return {"regret": round(float(chosen.sum() / best.sum() - 1.0), 5),
+            "mean_slowdown": round(float(np.mean(chosen / best)), 5),
+            "max_slowdown": round(float(np.max(chosen / best)), 4),
+            "exact": round(float(np.mean(chosen == best)), 4)}
+
+
+def run_selector(args, world, rank, local):
+    """Labels every synthetic matrix with the run-first tuner (time each format, keep the
+    fastest), trains the MLP selector on the 4/5 of seeds with seed % 5 != 0, and reports
+    its regret on the held-out fifth; then the 256^3 stencil end to end: the selector's
+    format with FP32 values and FP64 refinement against FP64 CG in the tuner's format."""
+    import torch
+    import paper_2304_09511_gb300 as mspv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    FMT = ("coo", "csr", "dia")
+    rec = []
+    t_label = time.perf_counter()
+    for seed in range(rank, args.matrices, world):
+        fam, n, r, c, v = synth.family_matrix_torch(seed, dev)
+        A = mspv.Matrix.from_coo(n, n, r, c, v)
+        del r, c, v
+        nnz = A.info["nnz"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = A.features()
+        t_feat = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        best, ms = A.tune_format(reps=args.tune_reps)
+        t_tune = time.perf_counter() - t0
+        A.close()
+        rec.append({"seed": seed, "family": fam, "n": n, "nnz": nnz, "features": f.tolist(),
+                    "ms": [ms[k] for k in FMT], "best": FMT.index(best), "t_feat": t_feat, "t_tune": t_tune})
+    t_label = time.perf_counter() - t_label
+    if world > 1:
+        import torch.distributed as dist
+        allrec = [None] * world
+        dist.all_gather_object(allrec, rec)
+        rec = sorted((x for part in allrec for x in part), key=lambda x: x["seed"])
+        t_label = max_over_ranks(t_label, world)
+    out = None
+    if rank == 0:
+        X = np.array([x["features"] for x in rec], dtype=np.float32)
+        y = np.array([x["best"] for x in rec], dtype=np.int32)
+        ms = np.array([x["ms"] for x in rec], dtype=np.float64)
+        held = np.array([x["seed"] % 5 == 0 for x in rec])
+        t0 = time.perf_counter()
+        params = mspv.selector_train(X[~held], y[~held], epochs=args.epochs, lr=args.lr, seed=0)
+        t_train = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pred = mspv.selector_predict(params, X[held])
+        t_pred = time.perf_counter() - t0
+        # a DIA pick the tuner could not build (inf) counts as CSR, as mspv_select_format does
+        pred = np.where(np.isinf(ms[held][np.arange(held.sum()), pred]), 1, pred)
+        train_acc = float(np.mean(mspv.selector_predict(params, X[~held]) == y[~held]))
+        fams = np.array([x["family"] for x in rec])
+        per_family = {}
+        for fam in synth.FAMILIES:
+            m = fams[held] == fam
+            if m.any():
+                per_family[fam] = {"n": int(m.sum()), "accuracy": round(float(np.mean(pred[m] == y[held][m])), 4),
+                                   "labels": np.bincount(y[held][m], minlength=3).tolist(),
+                                   **_regret(ms[held][m], pred[m])}
+        sel_stats = _regret(ms[held], pred)
+        csr_stats = _regret(ms[held], np.ones(int(held.sum()), dtype=np.int64))
+        t_feat = np.array([x["t_feat"] for x in rec])
+        t_tune = np.array([x["t_tune"] for x in rec])
+        out = {
+            "metric": SELECTOR_METRIC, "value": sel_stats["regret"], "unit": "fraction",
+            "higher_is_better": False, "n_gpus": world, "mode": "selector", "data": "synthetic",
+            "dtype": "f32 (MLP), f64 (SpMV timing)",
+            "config": {"workload": f"{args.matrices} seeded matrices, 4 families (banded, uniform 8-64/row, "
+                                   "power-law rows, 32x32 block-diagonal), n log-uniform in [1e4, 2e6]; "
+                                   f"train seed % 5 != 0 ({int((~held).sum())}), held out seed % 5 == 0 "
+                                   f"({int(held.sum())}); labels: run-first tuner, {args.tune_reps} timed "
+                                   "SpMV per format; MLP 10-64-64-3, Adam",
+                       "epochs": args.epochs, "lr": args.lr, "parallelism": f"labels sharded x{world}"},
+            "held_out": {**sel_stats, "accuracy": round(float(np.mean(pred == y[held])), 4),
+                         "always_csr": csr_stats, "per_family": per_family},
+            "train_accuracy": round(train_acc, 4),
+            "label_distribution": {FMT[k]: int(v) for k, v in enumerate(np.bincount(y, minlength=3))},
+            "cost_ms_per_matrix": {"features": round(float(t_feat.mean() * 1e3), 3),
+                                   "predict_batch_total": round(t_pred * 1e3, 3),
+                                   "run_first_tuner": round(float(t_tune.mean() * 1e3), 3)},
+            "train_s": round(t_train, 3), "label_s": round(t_label, 2),
+        }
+        if args.e2e_grid > 0:
+            out["stencil_e2e"] = _selector_stencil_e2e(mspv, torch, dev, params, args.e2e_grid)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def _selector_stencil_e2e(mspv, torch, dev, params, g):
+    """Time-to-1e-10 on the g^3 stencil (b = A 1, x0 = 0): FP64 CG in the tuner's format,
+    and FP32-value refinement (FP32-arithmetic inner CG) in the selector's format."""
+    n = g ** 3
+    r, c, v = synth.stencil27_torch(g, dev)
+    A = mspv.Matrix.from_coo(n, n, r, c, v)
+    del r, c, v
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    pick = A.select_format(params)
+    t_select = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tuned, tms = A.tune_format(reps=10)
+    t_tune = time.perf_counter() - t0
+    res = {"grid": g, "n": n, "nnz": A.info["nnz"], "selector_format": pick, "tuner_format": tuned,
+           "tuner_ms_per_spmv": {k: round(x, 5) for k, x in tms.items()},
+           "select_s": round(t_select, 4), "tune_s": round(t_tune, 3)}
+    M64 = {f: (A if f == "coo" else A.convert(f)) for f in {pick, tuned}}
+    Mlo = A.convert(pick, "f32")
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    b = M64[tuned].spmv(ones)
+    os.environ["MSPV_CG_CHECK_EVERY"] = "10"
+
+    def timed(fn):
+        xx = torch.zeros(n, dtype=torch.float64, device=dev)
+        fn(xx)
+        xx.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        out = fn(xx)
+        e.record(stream)
+        torch.cuda.synchronize()
+        err = float((xx - 1.0).abs().max().item())
+        return {"ms": round(s.elapsed_time(e), 2), "iters": out.iters, "outer": out.outer_iters,
+                "relres": out.relres, "converged": out.converged, "max_abs_err_vs_x1": err}
+
+    res["fp64_cg_tuner_format"] = timed(lambda xx: M64[tuned].cg(b, x=xx, tol=1e-10, maxit=20000))
+    if pick != tuned:
+        res["fp64_cg_selector_format"] = timed(lambda xx: M64[pick].cg(b, x=xx, tol=1e-10, maxit=20000))
+    if Mlo is not None:
+        res["ir_f32_values_fp32_inner_selector_format"] = timed(
+            lambda xx: M64[pick].cg_ir(Mlo, b, x=xx, tol=1e-10, inner_tol=1e-4, max_outer=30,
+                                       maxit_inner=20000, inner_fp32=True))
+    return res
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 def oracle_workload(g):
@@ -412,12 +565,23 @@ def main():
     ap.add_argument("--ref-cg-iters", type=int, default=1,
                     help="CG iterations per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["step", "selector"], default="step",
+                    help="step: the SpMV + CG step (default); selector: tuner labels, MLP "
+                         "training and held-out regret, then the stencil end to end")
+    ap.add_argument("--matrices", type=int, default=2000, help="selector mode: synthetic matrices")
+    ap.add_argument("--tune-reps", type=int, default=10, help="selector mode: timed SpMV per format")
+    ap.add_argument("--epochs", type=int, default=300, help="selector mode: training epochs")
+    ap.add_argument("--lr", type=float, default=1e-3, help="selector mode: Adam step size")
+    ap.add_argument("--e2e-grid", type=int, default=256,
+                    help="selector mode: stencil grid of the end-to-end solve (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mspv":
         args.warmup = 3
     world, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, world, rank)
+    elif args.mode == "selector":
+        out = run_selector(args, world, rank, local)
     else:
         out = run_mspv(args, world, rank, local)
     if out is not None:

@@ -186,6 +186,76 @@ MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t ncols, int64_t
                                            const double* vals, const double* x, double* y,
                                            void* stream);
 
+/*
+ * ---- Format selection ----
+ * The paper's distributed HPCG chooses each process's format with a run-first auto-tuner
+ * (Sec. VI: time every format, keep the fastest), and its related work cites learned
+ * selectors (Sec. VII). mspv_tune_format is the run-first tuner; the features and the
+ * small FP32 MLP below are a learned selector trained on its labels, so that a format
+ * can be chosen without building and timing all three.
+ */
+#define MSPV_NUM_FEATURES 10
+#define MSPV_SELECTOR_PARAMS 5079
+
+/*
+ * The sparsity features of A's stored structure, rounded to FP32, into HOST out[10]:
+ *   0 log2 max(nrows, 1)            5 shortest row (entries)
+ *   1 log2 max(nnz, 1)              6 log2 max(ndiags, 1), ndiags = distinct col - row
+ *   2 mean row length nnz / nrows   7 DIA fill nnz / (ndiags * nrows) (0 if ndiags = 0)
+ *   3 population std of row length  8 empty rows / nrows
+ *   4 longest row (entries)         9 max |col - row| / nrows
+ * Row-based entries are 0 for nrows = 0. Counts are taken on the device (integers); the
+ * ratios are formed in FP64 on the host. Any format. Synchronous.
+ */
+MSPV_API mspv_status mspv_features(mspv_matrix_t A, float* out, void* stream);
+
+/*
+ * Run-first tuner: builds A in each other format (FP64 values), times `reps` SpMV launches
+ * of each (x = 1, after two warm-up launches) with CUDA events on `stream`, frees the copies,
+ * and writes the mean milliseconds per SpMV to HOST ms[3] (indexed by mspv_format; +inf for
+ * DIA when A is not square or DIA storage would exceed its fill cap) and the fastest format
+ * to *best. Ties: starting from CSR, then DIA, then COO, a format replaces the current
+ * choice only when it is more than 1% faster. A must be a COO or CSR handle (EFORMAT for
+ * DIA); reps >= 1. Synchronous; the temporary handles are allocated and freed inside.
+ */
+MSPV_API mspv_status mspv_tune_format(mspv_matrix_t A, int32_t reps, void* stream, double* ms,
+                                      mspv_format* best);
+
+/*
+ * Trains the selector MLP (10 -> 64 -> 64 -> 3, ReLU, softmax cross-entropy; class k is
+ * mspv_format k) in one CTA on HOST features X[N * 10] (row-major, as mspv_features writes
+ * them) and HOST labels y[N] in {0, 1, 2}. Features are standardised by the training set's
+ * mean and population standard deviation (1 where that is below 1e-6). Weights start as
+ * uniform Glorot values drawn from SplitMix64 output k (seed `seed`) for trained parameter k
+ * in layout order, biases at 0. Each epoch runs Adam (Kingma & Ba 2015: beta1 0.9, beta2
+ * 0.999, eps 1e-8, step size lr) over minibatches of 64 consecutive samples in index order
+ * (the last one may be shorter), each gradient the mean over its minibatch. Writes
+ * MSPV_SELECTOR_PARAMS floats to HOST params in the layout
+ *   mu[10] sd[10] W1[64][10] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]   (W[out][in]).
+ * Deterministic (fixed summation order). EINVAL for N < 1, epochs < 0, lr <= 0 or a label
+ * outside {0, 1, 2}. Synchronous.
+ */
+MSPV_API mspv_status mspv_selector_train(const float* X, const int32_t* y, int32_t N,
+                                         int32_t epochs, float lr, uint64_t seed, float* params,
+                                         void* stream);
+
+/*
+ * Predicted class for each row of HOST features X[N * 10] under HOST params (the layout
+ * above): arg max of the logits, the lowest class on ties; into HOST out[N]. N >= 0.
+ * Synchronous.
+ */
+MSPV_API mspv_status mspv_selector_predict(const float* params, const float* X, int32_t N,
+                                           int32_t* out, void* stream);
+
+/*
+ * The format to use for A. params == NULL: the run-first tuner (mspv_tune_format, 10
+ * reps; A must be COO or CSR). Otherwise the MLP on mspv_features(A); a DIA prediction for
+ * a matrix that is not square or whose DIA storage would exceed the fill cap becomes CSR.
+ * Synchronous.
+ */
+MSPV_API mspv_status mspv_select_format(mspv_matrix_t A, const float* params, void* stream,
+                                        mspv_format* best);
+
 /* Fill *info with the handle's shape, format and row statistics. */
 MSPV_API mspv_status mspv_info(mspv_matrix_t A, mspv_matrix_info* info);
 

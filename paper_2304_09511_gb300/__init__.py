@@ -22,7 +22,11 @@ from . import _lib
 from ._lib import MspvError, FORMATS, VALUE_TYPES, load
 
 __all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "stream_handle",
-           "spmv_coo_noalloc"]
+           "spmv_coo_noalloc", "selector_train", "selector_predict", "NUM_FEATURES",
+           "SELECTOR_PARAMS"]
+
+NUM_FEATURES = _lib.NUM_FEATURES
+SELECTOR_PARAMS = _lib.SELECTOR_PARAMS
 
 _FMT_NAMES = {v: k for k, v in FORMATS.items()}
 _VT_NAMES = {v: k for k, v in VALUE_TYPES.items()}
@@ -180,6 +184,32 @@ class Matrix:
         _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
         return CgResult(x, st, it.value, rr.value)
 
+    def features(self, stream=None) -> np.ndarray:
+        """The ten FP32 sparsity features of the stored structure (mspv_features)."""
+        out = np.zeros(NUM_FEATURES, dtype=np.float32)
+        _lib.check(load().mspv_features(self._h, out.ctypes.data, stream_handle(stream)))
+        return out
+
+    def tune_format(self, reps: int = 10, stream=None):
+        """Run-first tuner: (best format name, {format: ms per SpMV}); inf where DIA is not
+        built (not square, or over its fill cap)."""
+        ms = np.zeros(3, dtype=np.float64)
+        best = ctypes.c_int(0)
+        _lib.check(load().mspv_tune_format(self._h, int(reps), stream_handle(stream), ms.ctypes.data,
+                                           ctypes.byref(best)))
+        return _FMT_NAMES[best.value], {_FMT_NAMES[k]: float(ms[k]) for k in range(3)}
+
+    def select_format(self, params=None, stream=None) -> str:
+        """Format chosen by the MLP `params` (float32[SELECTOR_PARAMS]), or by the run-first
+        tuner when params is None."""
+        best = ctypes.c_int(0)
+        pp = None
+        if params is not None:
+            params = _params_array(params)
+            pp = params.ctypes.data
+        _lib.check(load().mspv_select_format(self._h, pp, stream_handle(stream), ctypes.byref(best)))
+        return _FMT_NAMES[best.value]
+
     def cg_ir(self, low: "Matrix", b, x=None, tol: float = 1e-10, inner_tol: float = 1e-6,
               max_outer: int = 50, maxit_inner: int = 10000, inner_fp32: bool = False,
               stream=None) -> CgResult:
@@ -198,6 +228,43 @@ class Matrix:
                                      ctypes.byref(rr))
         _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
         return CgResult(x, st, ii.value, rr.value, outer_iters=oi.value)
+
+
+def _params_array(params) -> np.ndarray:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.shape != (SELECTOR_PARAMS,):
+        raise ValueError(f"selector parameters must have {SELECTOR_PARAMS} entries")
+    return p
+
+
+def _features_array(X) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    if X.ndim != 2 or X.shape[1] != NUM_FEATURES:
+        raise ValueError(f"features must be an (N, {NUM_FEATURES}) array")
+    return X
+
+
+def selector_train(X, y, epochs: int = 200, lr: float = 1e-3, seed: int = 0, stream=None) -> np.ndarray:
+    """Train the format-selector MLP on the GPU (mspv_selector_train); returns the
+    float32[SELECTOR_PARAMS] parameter vector."""
+    X = _features_array(X)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    if y.shape != (X.shape[0],):
+        raise ValueError("one label per feature row")
+    out = np.zeros(SELECTOR_PARAMS, dtype=np.float32)
+    _lib.check(load().mspv_selector_train(X.ctypes.data, y.ctypes.data, int(X.shape[0]), int(epochs),
+                                          float(lr), int(seed), out.ctypes.data, stream_handle(stream)))
+    return out
+
+
+def selector_predict(params, X, stream=None) -> np.ndarray:
+    """Predicted format index (0 COO, 1 CSR, 2 DIA) per feature row (mspv_selector_predict)."""
+    params = _params_array(params)
+    X = _features_array(X)
+    out = np.zeros(X.shape[0], dtype=np.int32)
+    _lib.check(load().mspv_selector_predict(params.ctypes.data, X.ctypes.data, int(X.shape[0]),
+                                            out.ctypes.data, stream_handle(stream)))
+    return out
 
 
 def _as_contig(a, dtype):

@@ -53,7 +53,15 @@ SIGNATURES = {
     "mspv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mspv_csr_vector_width": (i32, [dbl, dbl, i32]),
     "mspv_version": (i32, []),
+    "mspv_features": (i32, [vp, vp, vp]),
+    "mspv_tune_format": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int)]),
+    "mspv_selector_train": (i32, [vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]),
+    "mspv_selector_predict": (i32, [vp, vp, i32, vp, vp]),
+    "mspv_select_format": (i32, [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
 }
+
+NUM_FEATURES = 10
+SELECTOR_PARAMS = 5079
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:

@@ -262,4 +262,61 @@ MSPV_API mspv_status mspv_export(mspv_matrix_t A, int32_t* idx0, int32_t* idx1, 
     MSPV_GUARD_END
 }
 
+MSPV_API mspv_status mspv_features(mspv_matrix_t A, float* out, void* stream) {
+    MSPV_GUARD_BEGIN
+    if (!A || !out) return set_error(MSPV_EINVAL, "features: NULL argument");
+    MSPV_TRY(compute_features(A, out, as_stream(stream)));
+    clear_error();
+    return MSPV_OK;
+    MSPV_GUARD_END
+}
+
+MSPV_API mspv_status mspv_tune_format(mspv_matrix_t A, int32_t reps, void* stream, double* ms,
+                                      mspv_format* best) {
+    MSPV_GUARD_BEGIN
+    if (!A || !ms || !best) return set_error(MSPV_EINVAL, "tune_format: NULL argument");
+    if (reps < 1) return set_error(MSPV_EINVAL, "tune_format: reps = %d < 1", reps);
+    int32_t b = MSPV_CSR;
+    MSPV_TRY(tune_formats(A, reps, as_stream(stream), ms, &b));
+    *best = (mspv_format)b;
+    return MSPV_OK;
+    MSPV_GUARD_END
+}
+
+MSPV_API mspv_status mspv_selector_train(const float* X, const int32_t* y, int32_t N, int32_t epochs, float lr,
+                                         uint64_t seed, float* params, void* stream) {
+    MSPV_GUARD_BEGIN
+    if (!X || !y || !params) return set_error(MSPV_EINVAL, "selector_train: NULL argument");
+    if (N < 1 || epochs < 0 || !(lr > 0.0f))
+        return set_error(MSPV_EINVAL, "selector_train: N = %d, epochs = %d, lr = %g", N, epochs, (double)lr);
+    for (int32_t i = 0; i < N; ++i)
+        if (y[i] < 0 || y[i] > 2) return set_error(MSPV_EINVAL, "selector_train: label %d of sample %d", y[i], i);
+    MSPV_TRY(selector_train(X, y, N, epochs, lr, seed, params, as_stream(stream)));
+    clear_error();
+    return MSPV_OK;
+    MSPV_GUARD_END
+}
+
+MSPV_API mspv_status mspv_selector_predict(const float* params, const float* X, int32_t N, int32_t* out,
+                                           void* stream) {
+    MSPV_GUARD_BEGIN
+    if (N < 0) return set_error(MSPV_EINVAL, "selector_predict: N = %d", N);
+    if (!params || (N > 0 && (!X || !out))) return set_error(MSPV_EINVAL, "selector_predict: NULL argument");
+    MSPV_TRY(selector_predict(params, X, N, out, as_stream(stream)));
+    clear_error();
+    return MSPV_OK;
+    MSPV_GUARD_END
+}
+
+MSPV_API mspv_status mspv_select_format(mspv_matrix_t A, const float* params, void* stream, mspv_format* best) {
+    MSPV_GUARD_BEGIN
+    if (!A || !best) return set_error(MSPV_EINVAL, "select_format: NULL argument");
+    int32_t b = MSPV_CSR;
+    MSPV_TRY(select_format(A, params, as_stream(stream), &b));
+    *best = (mspv_format)b;
+    clear_error();
+    return MSPV_OK;
+    MSPV_GUARD_END
+}
+
 }  // extern "C"

@@ -386,29 +386,32 @@ struct RowStats {
     unsigned long long sum_sq;
     unsigned long long empty;
     int32_t max;
-    int32_t pad;
+    int32_t min;
 };
 
 __global__ void row_stats_kernel(const int32_t* __restrict__ counts, int32_t n, RowStats* st) {
     unsigned long long sq = 0, empty = 0;
-    int32_t mx = 0;
+    int32_t mx = 0, mn = INT32_MAX;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t c = counts[i];
         sq += (unsigned long long)c * (unsigned long long)c;
         empty += (c == 0);
         mx = max(mx, c);
+        mn = min(mn, c);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sq += __shfl_xor_sync(0xffffffffu, sq, o);
         empty += __shfl_xor_sync(0xffffffffu, empty, o);
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&st->sum_sq, sq);
         atomicAdd(&st->empty, empty);
         atomicMax(&st->max, mx);
+        atomicMin(&st->min, mn);
     }
 }
 
@@ -420,6 +423,8 @@ static mspv_status compute_row_stats(const int32_t* ai, int64_t nnz, int32_t nro
     MSPV_TRY(stats.alloc(sizeof(RowStats)));
     MSPV_CUDA_TRY(cudaMemsetAsync(counts.ptr, 0, sizeof(int32_t) * ((size_t)nrows + 1), s));
     MSPV_CUDA_TRY(cudaMemsetAsync(stats.ptr, 0, sizeof(RowStats), s));
+    const int32_t big = INT32_MAX;
+    MSPV_CUDA_TRY(cudaMemcpyAsync(&stats.as<RowStats>()->min, &big, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (nnz > 0) {
         row_count_kernel<<<grid_for(nnz), kThreads, 0, s>>>(ai, nnz, counts.as<int32_t>());
         MSPV_CUDA_TRY(cudaGetLastError());
@@ -437,6 +442,7 @@ static mspv_status compute_row_stats(const int32_t* ai, int64_t nnz, int32_t nro
     double var = (double)h.sum_sq / n - M->row_mean * M->row_mean;
     M->row_std = std::sqrt(var > 0.0 ? var : 0.0);
     M->row_max = h.max;
+    M->row_min = nrows > 0 ? h.min : 0;
     M->empty_rows = (int64_t)h.empty;
     return MSPV_OK;
 }
@@ -494,6 +500,8 @@ static double dia_fill_cap() {
     return f > 0.0 ? f : 32.0;
 }
 
+double dia_slot_cap(int64_t nnz) { return std::fmax(dia_fill_cap() * (double)nnz, (double)(1 << 20)); }
+
 mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStream_t s,
                        mspv_matrix* M) {
     if (A->format == MSPV_DIA)
@@ -506,6 +514,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
     M->row_mean = A->row_mean;
     M->row_std = A->row_std;
     M->row_max = A->row_max;
+    M->row_min = A->row_min;
     M->empty_rows = A->empty_rows;
     const int64_t nnz = A->nnz;
     const size_t vs = value_size(vt);
@@ -577,7 +586,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
     const int32_t npad = ((n + 31) / 32) * 32;
     const double slots = (double)nd * (double)npad;
-    const double cap = std::fmax(dia_fill_cap() * (double)nnz, (double)(1 << 20));
+    const double cap = dia_slot_cap(nnz);
     if (slots > cap)
         return set_error(MSPV_ETOOBIG, "convert: DIA would store %d diagonals x %d rows = %.0f slots for %lld entries (cap %.0f)",
                          nd, npad, slots, (long long)nnz, cap);

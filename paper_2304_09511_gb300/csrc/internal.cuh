@@ -144,7 +144,7 @@ struct CooCarry {
 // Entries per CTA window of the staged COO and CSR kernels: values and gathered x are
 // staged in shared memory (16 B per entry, plus 4 B of row index for COO).
 constexpr int kCooWindow = 3072;    // staged COO kernel (allocation-free entry point)
-constexpr int kCooVecChunk = 1024;  // run-vector COO kernel: entries per warp
+constexpr int kCooVecChunk = 256;   // run-vector COO kernel: entries per warp
 constexpr int kCsrWindow = 2560;     // a CTA takes the rows that start in its window
 
 // CG workspace, owned by a handle and grown on demand.
@@ -189,6 +189,7 @@ struct mspv_matrix {
     int32_t csr_vector = 0;   // 0: staged kernel; 1..32: lanes per row
     int32_t csr_block = 0;    // staged kernel: 0 = warp-private staging, 1 = CTA row blocks
     int32_t row_max = 0;
+    int32_t row_min = 0;
     double row_mean = 0.0, row_std = 0.0;
     int64_t empty_rows = 0;
     int device = 0;
@@ -224,6 +225,8 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
 mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, double* vals,
                           cudaStream_t s);
 void free_matrix(mspv_matrix* M);
+// DIA slots (ndiags * npad) allowed for nnz entries: max(MSPV_DIA_MAX_FILL (32) * nnz, 2^20)
+double dia_slot_cap(int64_t nnz);
 mspv_status ensure_coo_carry(mspv_matrix* M);
 mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
 
@@ -250,6 +253,17 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
                         double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
                         int32_t inner_fp32, cudaStream_t s, int32_t* outer_iters,
                         int32_t* inner_iters, double* relres);
+
+// select.cu: format selection features, run-first tuner, MLP selector
+constexpr int kSelectorFeatures = 10;
+constexpr int kSelectorParams = 5079;   // mu, sd, W1, b1, W2, b2, W3, b3
+mspv_status compute_features(const mspv_matrix* A, float* out, cudaStream_t s, int64_t* ndiags = nullptr);
+mspv_status select_format(const mspv_matrix* A, const float* params, cudaStream_t s, int32_t* best);
+mspv_status tune_formats(const mspv_matrix* A, int32_t reps, cudaStream_t s, double* ms, int32_t* best);
+mspv_status selector_train(const float* X, const int32_t* y, int32_t N, int32_t epochs, float lr,
+                           uint64_t seed, float* params, cudaStream_t s);
+mspv_status selector_predict(const float* params, const float* X, int32_t N, int32_t* out,
+                             cudaStream_t s);
 
 // block-wide reductions shared by the kernels (defined inline below)
 __device__ __forceinline__ double warp_sum(double v) {

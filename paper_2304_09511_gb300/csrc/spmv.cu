@@ -708,15 +708,13 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
 }
 
 // COO, run-vector kernel. Warp c takes the chunk of kCooVecChunk sorted entries
-// [c*C, (c+1)*C). Pass 1 (integer only): lanes read the row indices 256 at a time
-// (coalesced), mark where the row changes, and compact the run starts with ballots into
-// the warp's slice of shared memory, zeroing the rows skipped between runs. Pass 2:
-// groups of 4 lanes take one run each, lane-strided FMAs over its entries, then 2
-// shuffle-adds -- the CSR V = 4 pattern, which on GB300 balances coalescing against FP64
-// issue slots. 1024-entry chunks hold ~39 runs of the 27-point stencil, so the 8-run
-// passes are nearly full (a partly idle pass costs a full FP64 issue slot). Runs cut by
-// a chunk edge leave partial sums in the carry record, added by the fix-up pass.
-constexpr int kCooVecSub = 256;   // row indices read per pass-1 step
+// [c*C, (c+1)*C). Pass 1 (integer only): lanes read the row indices (coalesced), mark
+// where the row changes, and compact the run starts with ballots into the warp's slice
+// of shared memory, zeroing the rows skipped between runs. Pass 2: groups of 4 lanes
+// take one run each, lane-strided FMAs over its entries, then 2 shuffle-adds -- the CSR
+// V = 4 pattern, which on GB300 balances coalescing against FP64 issue slots. Runs cut
+// by a chunk edge leave partial sums in the carry record, added by the fix-up pass.
+constexpr int kCooVecPer = kCooVecChunk / 32;
 
 template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
@@ -725,6 +723,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     int64_t nchunks, const CgState* st) {
     if (st && st->done) return;
     __shared__ int32_t s_rs[kThreads / 32][kCooVecChunk + 1];
+    __shared__ int32_t s_row[kThreads / 32][kCooVecChunk];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + w;
@@ -733,50 +732,46 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     const int len = (int)((nnz - c0 < kCooVecChunk) ? nnz - c0 : kCooVecChunk);
     const int32_t row_before = (c0 > 0) ? __ldg(ai + c0 - 1) : -1;
     const int32_t row_after = (c0 + len < nnz) ? __ldg(ai + c0 + len) : INT_MAX;
-    const int32_t* aic = ai + c0;
     int32_t* rs = s_rs[w];
+    int32_t* rrow = s_row[w];
 
+    int32_t rv[kCooVecPer];
+#pragma unroll
+    for (int q = 0; q < kCooVecPer; ++q) {
+        const int k = q * 32 + lane;
+        rv[q] = (k < len) ? __ldcs(ai + c0 + k) : INT_MAX;
+    }
     int nr = 0;
     int32_t carry_row = row_before;
-    for (int sub0 = 0; sub0 < len; sub0 += kCooVecSub) {
-        int32_t rv[kCooVecSub / 32];
 #pragma unroll
-        for (int q = 0; q < kCooVecSub / 32; ++q) {
-            const int k = sub0 + q * 32 + lane;
-            rv[q] = (k < len) ? __ldg(aic + k) : INT_MAX;
+    for (int q = 0; q < kCooVecPer; ++q) {
+        const int k = q * 32 + lane;
+        const int32_t r = rv[q];
+        int32_t prev = __shfl_up_sync(FULL, r, 1);
+        if (lane == 0) prev = carry_row;
+        const bool start = (k < len) && (k == 0 || r != prev);
+        const unsigned ballot = __ballot_sync(FULL, start);
+        if (start) {
+            const int pos = nr + __popc(ballot & ((1u << lane) - 1u));
+            rs[pos] = k;
+            rrow[pos] = r;
+            if (r != prev)
+                for (int32_t z = prev + 1; z < r; ++z) y[z] = T(0);   // empty rows in between
         }
-#pragma unroll
-        for (int q = 0; q < kCooVecSub / 32; ++q) {
-            const int k = sub0 + q * 32 + lane;
-            const int32_t r = rv[q];
-            int32_t prev = __shfl_up_sync(FULL, r, 1);
-            if (lane == 0) prev = carry_row;
-            const bool start = (k < len) && (k == 0 || r != prev);
-            const unsigned ballot = __ballot_sync(FULL, start);
-            if (start) {
-                rs[nr + __popc(ballot & ((1u << lane) - 1u))] = k;
-                if (r != prev)
-                    for (int32_t z = prev + 1; z < r; ++z) y[z] = T(0);   // empty rows in between
-            }
-            nr += __popc(ballot);
-            carry_row = __shfl_sync(FULL, r, 31);
-        }
+        nr += __popc(ballot);
+        carry_row = __shfl_sync(FULL, r, 31);
     }
     if (lane == 0) rs[nr] = len;
     __syncwarp();
 
-    const int32_t row_first = __ldg(aic);
-    const int32_t row_last = __ldg(aic + len - 1);
-    const bool cont_prev = (row_before == row_first);
-    const bool cont_next = (row_after == row_last);
+    const bool cont_prev = (row_before == rrow[0]);
+    const bool cont_next = (row_after == rrow[nr - 1]);
     const int grp = lane >> 2, sub = lane & 3;
     for (int i0 = 0; i0 < nr; i0 += 8) {
         const int i = i0 + grp;
         T sum = T(0);
-        int b = 0;
         if (i < nr) {
-            b = rs[i];
-            const int e = rs[i + 1];
+            const int b = rs[i], e = rs[i + 1];
             for (int j = b + sub; j < e; j += 4)
                 sum = fma_t(convert_value<T>(__ldcs(av + c0 + j)), __ldg(x + __ldcs(aj + c0 + j)), sum);
         }
@@ -787,15 +782,15 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
             const bool to_tail = (i == nr - 1) && cont_next;
             if (to_head) carry[c].head = to_f64_exact(sum);
             if (to_tail) carry[c].tail = to_f64_exact(sum);
-            if (!to_head && !to_tail) y[__ldg(aic + b)] = sum;
+            if (!to_head && !to_tail) y[rrow[i]] = sum;
         }
     }
     if (lane == 0) {
-        carry[c].row_first = row_first;
-        carry[c].row_last = row_last;
+        carry[c].row_first = rrow[0];
+        carry[c].row_last = rrow[nr - 1];
     }
     if (c0 + len == nnz)   // empty rows after the last entry
-        for (int32_t z = row_last + 1 + lane; z < nrows; z += 32) y[z] = T(0);
+        for (int32_t z = rrow[nr - 1] + 1 + lane; z < nrows; z += 32) y[z] = T(0);
 }
 
 // Rows spanning windows: the window where such a row starts adds its tail, the heads of

@@ -92,6 +92,39 @@ def stencil27(g: int, perturb_seed: int | None = None, planes_per_chunk: int = 1
     return rows, cols, vals
 
 
+def stencil27_torch(g: int, device, planes_per_chunk: int = 32):
+    """The unperturbed 27-point stencil of stencil27, built by torch on `device` (same
+    triplets, same (row, col) order): for grids whose host generation would be slow."""
+    import torch
+    n = g * g * g
+    nnz = stencil_nnz(g)
+    kw = {"device": device}
+    rows = torch.empty(nnz, dtype=torch.int32, **kw)
+    cols = torch.empty(nnz, dtype=torch.int32, **kw)
+    vals = torch.empty(nnz, dtype=torch.float64, **kw)
+    off = torch.tensor([dz * g * g + dy * g + dx for dz, dy, dx in _OFFSETS], dtype=torch.int64, **kw)
+    d = torch.tensor(_OFFSETS, dtype=torch.int64, **kw)          # (27, 3): dz, dy, dx
+    pos = 0
+    for z0 in range(0, g, planes_per_chunk):
+        z1 = min(g, z0 + planes_per_chunk)
+        r = torch.arange(z0 * g * g, z1 * g * g, dtype=torch.int64, **kw)
+        ix, iy, iz = r % g, (r // g) % g, r // (g * g)
+        jz = iz[:, None] + d[None, :, 0]
+        jy = iy[:, None] + d[None, :, 1]
+        jx = ix[:, None] + d[None, :, 2]
+        valid = (jx >= 0) & (jx < g) & (jy >= 0) & (jy < g) & (jz >= 0) & (jz < g)
+        C = r[:, None] + off[None, :]
+        rr = r[:, None].expand_as(C)[valid]
+        cc = C[valid]
+        cnt = rr.numel()
+        rows[pos:pos + cnt] = rr.to(torch.int32)
+        cols[pos:pos + cnt] = cc.to(torch.int32)
+        vals[pos:pos + cnt] = torch.where(rr == cc, 26.0, -1.0).to(torch.float64)
+        pos += cnt
+    assert pos == nnz
+    return rows, cols, vals
+
+
 def stencil27_perturbed(g: int, seed: int = 1):
     return stencil27(g, perturb_seed=seed)
 
@@ -144,3 +177,118 @@ def banded(n: int, k: int, seed: int, fill: float = 1.0, spread: int | None = No
     v = rng.uniform(-1.0, 1.0, r.size)
     p = rng.permutation(r.size)
     return r[p].astype(np.int32), c[p].astype(np.int32), v[p]
+
+
+# ---------------------------------------------------------------------------
+# Format-selector families: seeded matrices of four kinds, n log-uniform in
+# [n_min, n_max]. The family is seed % 4:
+#   0 banded: k in [5, 27] diagonals, symmetric offsets around 0 (DIA-friendly)
+#   1 uniform random rows: 8..64 entries per row, uniform columns (CSR-friendly)
+#   2 power-law rows: Pareto exponent in [1.8, 2.5], mean 16, at most 20,000 (COO-friendly)
+#   3 block diagonal: dense 32 x 32 blocks
+# Off-diagonal values U(-1, 1); the diagonal (where present) is sum |row| + 1.
+# ---------------------------------------------------------------------------
+FAMILIES = ("banded", "uniform", "powerlaw", "blockdiag")
+
+
+def family_spec(seed: int, n_min: int = 10_000, n_max: int = 2_000_000) -> dict:
+    """The scalar choices of selector sample `seed`: family, n (log-uniform in
+    [n_min, n_max]), and the family's parameter (banded: the diagonal offsets; power law:
+    the exponent), plus the numpy generator that continues the sample's stream."""
+    rng = np.random.default_rng(1_000_003 + seed)
+    fam = FAMILIES[seed % 4]
+    n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+    spec = {"family": fam, "n": n, "rng": rng}
+    if fam == "blockdiag":
+        spec["n"] = max(32, (n // 32) * 32)
+    elif fam == "banded":
+        k = int(rng.integers(5, 28))
+        half = (k - 1) // 2
+        span = int(rng.integers(half, 4 * half + 8)) + 1
+        ds = np.sort(rng.choice(np.arange(1, span + 1), half, replace=False))
+        offs = np.concatenate([-ds[::-1], [0], ds])
+        if offs.size < k:   # even k: one more positive offset
+            extra = np.setdiff1d(np.arange(1, span + 2), ds)[:1]
+            offs = np.sort(np.concatenate([offs, extra]))
+        spec["offsets"] = offs.astype(np.int64)
+    elif fam == "powerlaw":
+        spec["exponent"] = float(rng.uniform(1.8, 2.5))
+    return spec
+
+
+def family_matrix(seed: int, n_min: int = 10_000, n_max: int = 2_000_000):
+    """Returns (family name, n, rows, cols, vals) for selector sample `seed` (numpy, host).
+    Rows come out non-decreasing; columns are not sorted within a row."""
+    spec = family_spec(seed, n_min, n_max)
+    fam, n, rng = spec["family"], spec["n"], spec["rng"]
+    if fam == "banded":
+        rows, cols = [], []
+        for d in spec["offsets"].tolist():
+            i = np.arange(max(0, -d), min(n, n - d), dtype=np.int64)
+            rows.append(i)
+            cols.append(i + d)
+        r = np.concatenate(rows)
+        c = np.concatenate(cols)
+        order = np.argsort(r, kind="stable")
+        r, c = r[order], c[order]
+    elif fam == "uniform":
+        lens = rng.integers(8, 65, n)
+        r = np.repeat(np.arange(n, dtype=np.int64), lens)
+        c = rng.integers(0, n, r.size)
+    elif fam == "powerlaw":
+        a = spec["exponent"]
+        raw = (1.0 - rng.random(n)) ** (-1.0 / (a - 1.0))
+        lens = np.clip(np.floor(raw * (16.0 / raw.mean())), 1, 20_000).astype(np.int64)
+        r = np.repeat(np.arange(n, dtype=np.int64), lens)
+        c = rng.integers(0, n, r.size)
+    else:
+        r = np.repeat(np.arange(n, dtype=np.int64), 32)
+        c = (r // 32) * 32 + np.tile(np.arange(32, dtype=np.int64), n)
+    v = rng.uniform(-1.0, 1.0, r.size)
+    diag = r == c
+    if diag.any():
+        absrow = np.bincount(r, weights=np.abs(v), minlength=n)
+        v[diag] = absrow[r[diag]] + 1.0
+    return fam, n, r.astype(np.int32), c.astype(np.int32), v
+
+
+def family_matrix_torch(seed: int, device, n_min: int = 10_000, n_max: int = 2_000_000):
+    """The same families and sizes as family_matrix (same family_spec), with the bulk
+    arrays drawn by torch on `device` from a generator seeded with `seed` (so the draws
+    differ from the numpy ones; on one device type they are reproducible). For building
+    thousands of large samples where host generation would dominate.
+    Returns (family name, n, rows int32, cols int32, vals float64) as tensors on `device`."""
+    import torch
+    spec = family_spec(seed, n_min, n_max)
+    fam, n = spec["family"], spec["n"]
+    g = torch.Generator(device=device)
+    g.manual_seed(1_000_003 + seed)
+    kw = {"device": device}
+    if fam == "banded":
+        rows, cols = [], []
+        for d in spec["offsets"].tolist():
+            i = torch.arange(max(0, -d), min(n, n - d), dtype=torch.int64, **kw)
+            rows.append(i)
+            cols.append(i + d)
+        r = torch.cat(rows)
+        c = torch.cat(cols)
+        r, order = torch.sort(r, stable=True)
+        c = c[order]
+    elif fam in ("uniform", "powerlaw"):
+        if fam == "uniform":
+            lens = torch.randint(8, 65, (n,), generator=g, dtype=torch.int64, **kw)
+        else:
+            a = spec["exponent"]
+            u = torch.rand(n, generator=g, dtype=torch.float64, **kw)
+            raw = (1.0 - u) ** (-1.0 / (a - 1.0))
+            lens = torch.clamp(torch.floor(raw * (16.0 / raw.mean())), 1, 20_000).to(torch.int64)
+        r = torch.repeat_interleave(torch.arange(n, dtype=torch.int64, **kw), lens)
+        c = torch.randint(0, n, (r.numel(),), generator=g, dtype=torch.int64, **kw)
+    else:
+        r = torch.arange(n, dtype=torch.int64, **kw).repeat_interleave(32)
+        c = (r // 32) * 32 + torch.arange(32, dtype=torch.int64, **kw).repeat(n)
+    v = torch.rand(r.numel(), generator=g, dtype=torch.float64, **kw) * 2.0 - 1.0
+    diag = r == c
+    absrow = torch.zeros(n, dtype=torch.float64, **kw).index_add_(0, r, v.abs())
+    v = torch.where(diag, absrow[r] + 1.0, v)
+    return fam, n, r.to(torch.int32), c.to(torch.int32), v

@@ -109,3 +109,31 @@ def test_product_path_has_no_oracle_or_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_selector_entry_points_reject_bad_host_input(lib):
+    """Validation happens on the host, before any device work."""
+    import numpy as np
+    from paper_2304_09511_gb300 import _lib
+    X = np.zeros((4, _lib.NUM_FEATURES), dtype=np.float32)
+    params = np.zeros(_lib.SELECTOR_PARAMS, dtype=np.float32)
+    bad = np.array([0, 1, 3, 2], dtype=np.int32)
+    assert lib.mspv_selector_train(X.ctypes.data, bad.ctypes.data, 4, 1, 1e-3, 0, params.ctypes.data,
+                                   None) == _lib.EINVAL
+    assert b"label 3" in lib.mspv_last_error()
+    ok = np.array([0, 1, 2, 2], dtype=np.int32)
+    assert lib.mspv_selector_train(X.ctypes.data, ok.ctypes.data, 0, 1, 1e-3, 0, params.ctypes.data,
+                                   None) == _lib.EINVAL
+    assert lib.mspv_selector_train(X.ctypes.data, ok.ctypes.data, 4, 1, 0.0, 0, params.ctypes.data,
+                                   None) == _lib.EINVAL
+    assert lib.mspv_selector_train(None, ok.ctypes.data, 4, 1, 1e-3, 0, params.ctypes.data,
+                                   None) == _lib.EINVAL
+    out = np.zeros(4, dtype=np.int32)
+    assert lib.mspv_selector_predict(params.ctypes.data, X.ctypes.data, -1, out.ctypes.data,
+                                     None) == _lib.EINVAL
+    assert lib.mspv_selector_predict(None, X.ctypes.data, 4, out.ctypes.data, None) == _lib.EINVAL
+    fmt = ctypes.c_int(0)
+    ms = np.zeros(3)
+    assert lib.mspv_features(None, X.ctypes.data, None) == _lib.EINVAL
+    assert lib.mspv_tune_format(None, 10, None, ms.ctypes.data, ctypes.byref(fmt)) == _lib.EINVAL
+    assert lib.mspv_select_format(None, None, None, ctypes.byref(fmt)) == _lib.EINVAL

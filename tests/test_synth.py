@@ -1,0 +1,49 @@
+"""The seeded input generators: the torch stencil equals the numpy one, and the selector
+families have the shapes their recipe states."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("g", [2, 3, 7, 12])
+def test_torch_stencil_equals_numpy_stencil(g):
+    r, c, v = synth.stencil27(g)
+    rt, ct, vt = synth.stencil27_torch(g, "cpu", planes_per_chunk=5)
+    assert np.array_equal(r, rt.numpy()) and np.array_equal(c, ct.numpy())
+    assert np.array_equal(v, vt.numpy())
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("backend", ["numpy", "torch"])
+def test_family_recipe(seed, backend):
+    if backend == "numpy":
+        fam, n, r, c, v = synth.family_matrix(seed, n_min=1_000, n_max=20_000)
+    else:
+        fam, n, r, c, v = synth.family_matrix_torch(seed, "cpu", n_min=1_000, n_max=20_000)
+        r, c, v = r.numpy(), c.numpy(), v.numpy()
+    spec = synth.family_spec(seed, n_min=1_000, n_max=20_000)
+    assert fam == synth.FAMILIES[seed % 4] == spec["family"] and n == spec["n"]
+    assert 1_000 <= n <= 20_000 or fam == "blockdiag"
+    assert r.dtype == np.int32 and c.dtype == np.int32 and v.dtype == np.float64
+    assert np.all(np.diff(r) >= 0) and r.min() >= 0 and r.max() < n and c.min() >= 0 and c.max() < n
+    lens = np.bincount(r, minlength=n)
+    off = v[r != c]
+    assert np.all(np.abs(off) <= 1.0)
+    # diagonal entries dominate their rows (SPD-friendly values)
+    d = r == c
+    absrow = np.bincount(r, weights=np.abs(np.where(d, 0.0, v)), minlength=n)
+    assert np.all(v[d] > absrow[r[d]])
+    if fam == "banded":
+        offs = np.unique(c.astype(np.int64) - r)
+        assert 5 <= offs.size <= 27 and 0 in offs
+        assert np.array_equal(offs, spec["offsets"])
+    elif fam == "uniform":
+        assert lens.min() >= 8 and lens.max() <= 64
+    elif fam == "powerlaw":
+        assert lens.min() >= 1 and lens.max() <= 20_000
+        assert 10 <= lens.mean() <= 20
+    else:
+        assert np.all(lens == 32) and np.all(c // 32 == r // 32)
