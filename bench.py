@@ -226,7 +226,7 @@ def run_mspv(args, world, rank, local):
     cg_ms_iter = ms["cg"] / args.cg_iters
 
     # gpu launches of this library inside the timed region
-    coo_launches = 1 + (1 if (nnz + 255) // 256 > 1 else 0)
+    coo_launches = 1 + (1 if (nnz + 511) // 512 > 1 else 0)   # segment kernel + carry fix-up
     # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update
     launches_per_step = coo_launches + 1 + 1 + (3 + 5 * args.cg_iters)
 

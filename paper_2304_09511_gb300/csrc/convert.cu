@@ -4,6 +4,7 @@
 // every structure is bit-identical run to run. No kernel here waits on another CTA.
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <cmath>
 
 #include "internal.cuh"
@@ -615,6 +616,8 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
 
 mspv_status ensure_coo_carry(mspv_matrix* M) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
+    const char* k = std::getenv("MSPV_COO_KERNEL");
+    M->coo_kernel = (k && std::strcmp(k, "vec") == 0) ? 1 : 0;
     M->nchunks = (M->nnz + kCooVecChunk - 1) / kCooVecChunk;
     MSPV_TRY(dev_alloc_n(&M->carry, M->nchunks > 0 ? M->nchunks : 1));
     M->bytes += (M->nchunks > 0 ? M->nchunks : 1) * (int64_t)sizeof(CooCarry);

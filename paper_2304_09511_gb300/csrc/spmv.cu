@@ -819,6 +819,146 @@ __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_
     y[c.row_last] = (T)sum;
 }
 
+// ---------------------------------------------------------------------------
+// COO, lane-sequential segments
+// ---------------------------------------------------------------------------
+// A warp takes 512 consecutive (row-sorted) entries, each lane 16 of them in order: the
+// lane multiplies and accumulates sequentially (every FP64 FMA issued by all 32 lanes),
+// writes the rows that start and end inside its 16 entries, and keeps the partial sums of
+// its first run (head) and last run (tail). A head-flag segmented scan over the lanes' tail
+// sums (5 FP64 adds per warp) joins rows that span lanes; rows that span chunks leave the
+// same carry records as the other COO kernels for spmv_coo_fixup_kernel.
+constexpr int kCooSegPer = 16;
+constexpr int kCooSegChunk = 32 * kCooSegPer;
+static_assert(kCooSegChunk >= kCooVecChunk, "carry records are allocated for the smaller chunk");
+
+template <typename VT, typename T>
+__device__ __forceinline__ void load8_values(const VT* p, T (&v)[8]) {
+    using L = DiaVec<VT, T>;
+#pragma unroll
+    for (int q = 0; q < 8 / L::RPT; ++q) {
+        T t[L::RPT];
+        L::load(p + q * L::RPT, t);
+#pragma unroll
+        for (int k = 0; k < L::RPT; ++k) v[q * L::RPT + k] = t[k];
+    }
+}
+
+template <typename VT, typename T>
+__global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
+    int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
+    int64_t nchunks, const CgState* st) {
+    if (st && st->done) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    if (c >= nchunks) return;   // whole warp
+    const int64_t c0 = c * kCooSegChunk;
+    const int len = (int)((nnz - c0 < kCooSegChunk) ? nnz - c0 : kCooSegChunk);
+    const int32_t row_before = (c0 > 0) ? __ldg(ai + c0 - 1) : -1;
+    const int32_t row_after = (c0 + len < nnz) ? __ldg(ai + c0 + len) : INT_MAX;
+    const int32_t chunk_first = __ldg(ai + c0);
+    const int32_t chunk_last = __ldg(ai + c0 + len - 1);
+    const int b = lane * kCooSegPer;
+    const int cnt = (len - b >= kCooSegPer) ? kCooSegPer : (len - b > 0 ? len - b : 0);
+    const int64_t e0 = c0 + b;
+
+    // Sequential pass. `cur` starts at the row of the entry before the lane's first one, so
+    // the empty rows in between are zero-filled by the same row-change step. A lane without
+    // entries acts as a single run of the chunk's last row with sum 0 (transparent below).
+    int32_t cur = chunk_last, first = chunk_last;
+    T head = T(0), sum = T(0);
+    bool closed = false;   // the lane's first run has ended inside the lane
+    if (cnt > 0) {
+        cur = (e0 > 0) ? __ldg(ai + e0 - 1) : -1;
+        first = __ldg(ai + e0);
+#pragma unroll
+        for (int h = 0; h < kCooSegPer; h += 8) {
+            int32_t rr[8], jj[8];
+            T aa[8], xx[8];
+            if (cnt == kCooSegPer) {
+                const int4 r0 = __ldcs(reinterpret_cast<const int4*>(ai + e0 + h));
+                const int4 r1 = __ldcs(reinterpret_cast<const int4*>(ai + e0 + h + 4));
+                const int4 j0 = __ldcs(reinterpret_cast<const int4*>(aj + e0 + h));
+                const int4 j1 = __ldcs(reinterpret_cast<const int4*>(aj + e0 + h + 4));
+                rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w;
+                rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
+                jj[0] = j0.x; jj[1] = j0.y; jj[2] = j0.z; jj[3] = j0.w;
+                jj[4] = j1.x; jj[5] = j1.y; jj[6] = j1.z; jj[7] = j1.w;
+                load8_values<VT, T>(av + e0 + h, aa);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const bool ok = h + k < cnt;
+                    rr[k] = ok ? __ldcs(ai + e0 + h + k) : 0;
+                    jj[k] = ok ? __ldcs(aj + e0 + h + k) : 0;
+                    aa[k] = ok ? convert_value<T>(__ldcs(av + e0 + h + k)) : T(0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) xx[k] = (h + k < cnt) ? __ldg(x + jj[k]) : T(0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (h + k < cnt) {
+                    const int32_t r = rr[k];
+                    if (r != cur) {
+                        if (h + k > 0) {   // close run `cur`
+                            if (!closed) { head = sum; closed = true; }
+                            else y[cur] = sum;
+                        }
+                        for (int32_t z = cur + 1; z < r; ++z) y[z] = T(0);   // empty rows
+                        cur = r;
+                        sum = T(0);
+                    }
+                    sum = fma_t(aa[k], xx[k], sum);
+                }
+            }
+        }
+    }
+
+    // Segmented inclusive scan of the tail sums: a lane without an internal row change whose
+    // row equals the previous lane's last row continues that lane's last run.
+    const int32_t prev_last = __shfl_up_sync(FULL, cur, 1);
+    const bool cont = !closed && lane > 0 && first == prev_last;
+    T S = sum;
+    bool F = !cont;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T Su = __shfl_up_sync(FULL, S, d);
+        const bool Fu = __shfl_up_sync(FULL, F, d);
+        if (lane >= d) {
+            if (!F) S += Su;
+            F = F || Fu;
+        }
+    }
+    const T prevS = __shfl_up_sync(FULL, S, 1);
+    const int32_t next_first = __shfl_down_sync(FULL, first, 1);
+    const bool cp = (row_before == chunk_first);   // the chunk's first run started before it
+    const bool cn = (row_after == chunk_last);     // the chunk's last run continues after it
+
+    if (cnt > 0 && closed) {   // the lane's first run ends inside the lane
+        T tot = head;
+        if (lane > 0 && first == prev_last) tot += prevS;
+        if (first == chunk_first && cp) carry[c].head = to_f64_exact(tot);
+        else y[first] = tot;
+    }
+    if (lane < 31 && cnt > 0 && next_first != cur) {   // the last run ends at the lane's end
+        if (cur == chunk_first && cp) carry[c].head = to_f64_exact(S);
+        else y[cur] = S;
+    }
+    if (lane == 31) {   // S is the chunk's last run
+        const bool one_run = (chunk_first == chunk_last);
+        if (cn) carry[c].tail = to_f64_exact(S);
+        if (one_run && cp) carry[c].head = to_f64_exact(S);
+        if (!cn && !(one_run && cp)) y[chunk_last] = S;
+        carry[c].row_first = chunk_first;
+        carry[c].row_last = chunk_last;
+    }
+    if (c0 + len == nnz)   // empty rows after the last entry
+        for (int32_t z = chunk_last + 1 + lane; z < nrows; z += 32) y[z] = T(0);
+}
+
 template <typename T>
 __global__ void fill_zero_kernel(T* __restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -1054,9 +1194,16 @@ static void launch_coo_windows(int32_t nrows, int64_t nnz, const int32_t* ai, co
 
 template <typename VT, typename T>
 static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
-    const int64_t nch = A->nchunks;
-    spmv_coo_vec_kernel<VT, T><<<(unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(
-        A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, ep.st);
+    int64_t nch;
+    if (A->coo_kernel == 1) {
+        nch = A->nchunks;
+        spmv_coo_vec_kernel<VT, T><<<(unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(
+            A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, ep.st);
+    } else {
+        nch = (A->nnz + kCooSegChunk - 1) / kCooSegChunk;
+        spmv_coo_seg_kernel<VT, T><<<(unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(
+            A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, ep.st);
+    }
     if (nch > 1) spmv_coo_fixup_kernel<T><<<blocks_for(nch), kThreads, 0, s>>>(A->carry, nch, y, ep.st);
     if (ep.st)
         dot_alpha_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(A->nrows, x, y, ep);

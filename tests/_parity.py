@@ -26,6 +26,8 @@ def assert_spmv_parity(y_gpu, O, x, oracle):
     want = oracle.spmv(O, x)
     bound = spmv_tolerance(O, x, oracle)
     err = np.abs(y_gpu - want)
+    unwritten = np.nonzero(np.isnan(y_gpu) & ~np.isnan(want))[0]
+    assert unwritten.size == 0, f"{unwritten.size} rows NaN on the GPU, first {unwritten[0]}"
     bad = np.nonzero(err > bound)[0]
     assert bad.size == 0, (f"{bad.size} rows out of tolerance; first row {bad[0]}: "
                            f"gpu {y_gpu[bad[0]]!r} oracle {want[bad[0]]!r} bound {bound[bad[0]]:.3e}")

@@ -144,6 +144,38 @@ def test_csr_every_kernel_choice(mspv, orc, vec, monkeypatch):
     assert_spmv_parity(L.spmv(dev(x)).cpu().numpy(), OL, x, orc)
 
 
+@pytest.mark.parametrize("kernel", ["seg", "vec"])
+def test_coo_every_kernel_choice(mspv, orc, kernel, monkeypatch):
+    """Both COO kernels (lane-sequential 512-entry segments; run-vector 256-entry chunks) on
+    shapes that hit their edges: rows spanning lanes and chunks, a row covering many chunks,
+    empty rows before, between and after entries, partial last lanes and chunks, one entry."""
+    monkeypatch.setenv("MSPV_COO_KERNEL", kernel)
+    rng = np.random.default_rng(31)
+    shapes = []
+    n = 6000
+    lens = rng.choice([0, 1, 2, 15, 16, 17, 27, 31, 33, 511, 513, 1500], size=n,
+                      p=[.2, .1, .1, .1, .1, .1, .1, .05, .05, .04, .04, .02])
+    shapes.append((n, np.repeat(np.arange(n), lens)))
+    shapes.append((50, np.full(7000, 49)))                  # one row covering 14 chunks
+    shapes.append((3000, np.sort(rng.integers(1000, 1010, 1025))))   # empty rows both ends
+    shapes.append((100, np.array([37])))                     # a single entry
+    shapes.append((9000, np.repeat(np.arange(9000), 27)[: 512 * 7 + 5]))
+    for nr, r in shapes:
+        r = r.astype(np.int32)
+        c = rng.integers(0, nr, r.size).astype(np.int32)
+        v = rng.uniform(-1, 1, r.size)
+        for vt in ("f64", "f32"):
+            A = mspv.Matrix.from_coo(nr, nr, dev(r), dev(c), dev(v))
+            M = A if vt == "f64" else A.convert("coo", vt)
+            O = orc.canonicalize(nr, nr, r, c, v)
+            if vt != "f64":
+                O = orc.with_values(O, vt)
+            x = synth.uniform_x(nr, 4) * 2 - 1
+            y = torch.full((nr,), float("nan"), dtype=torch.float64, device="cuda")
+            M.spmv(dev(x), y)
+            assert_spmv_parity(y.cpu().numpy(), O, x, orc)
+
+
 def test_window_edges_of_staged_kernels(mspv, orc):
     """Rows cut by COO window edges (every 3072 entries) and CSR row blocks of every size
     agree with the oracle: long rows span several windows, short rows straddle edges."""
