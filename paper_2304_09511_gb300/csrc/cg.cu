@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(kThreads) cg_start_kernel(const double* __rest
 // alpha = rho / p.q, or a breakdown when p.q <= 0 or alpha is not finite.
 __global__ void __launch_bounds__(kThreads) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
                                                             CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     const double pq = sum_partials(partials, count);
     if (threadIdx.x == 0) finish_alpha(st, pq);
@@ -114,6 +116,8 @@ __global__ void __launch_bounds__(kThreads) cg_alpha_kernel(const double* __rest
 // rho' = r.r; stop when sqrt(rho') <= tol ||b||; beta = rho' / rho; iteration count.
 __global__ void __launch_bounds__(kThreads) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
                                                            CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     const double rr = sum_partials(partials, count);
     if (threadIdx.x == 0) {
@@ -159,6 +163,8 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
                                                              double* __restrict__ r, const double* __restrict__ p,
                                                              const double* __restrict__ q,
                                                              double* __restrict__ partials, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     const double alpha = st->alpha;
     double rr = 0.0;
@@ -174,6 +180,8 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
 // p = r + beta p
 __global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
                                                               double* __restrict__ p, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     const double beta = st->beta;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
@@ -245,6 +253,8 @@ __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* 
                                                               float* __restrict__ r, const float* __restrict__ p,
                                                               const float* __restrict__ q,
                                                               double* __restrict__ partials, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     __shared__ float s_alpha;
     if (threadIdx.x == 0) s_alpha = (float)st->alpha;
@@ -279,6 +289,8 @@ __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* 
 
 __global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, const float* __restrict__ r,
                                                                float* __restrict__ p, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     __shared__ float s_beta;
     if (threadIdx.x == 0) s_beta = (float)st->beta;
@@ -358,6 +370,13 @@ static mspv_status ensure_cg_work_f32(mspv_matrix* A) {
     return MSPV_OK;
 }
 
+// Programmatic dependent launches between the kernels of a CG iteration (MSPV_PDL=0 turns
+// them off): each kernel's launch overlaps the end of the previous one.
+static bool use_pdl() {
+    const char* s = std::getenv("MSPV_PDL");
+    return !(s && s[0] == '0');
+}
+
 static int check_every() {
     const char* s = std::getenv("MSPV_CG_CHECK_EVERY");
     const int v = s ? std::atoi(s) : 10;
@@ -373,7 +392,8 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
     CgState* hst = w.host_st;
     const int64_t n = A->nrows;
     const int64_t P = spmv_partials_needed(A);
-    const DotEpilogue ep{w.st, w.partials};
+    const bool pdl = use_pdl();
+    const DotEpilogue ep{w.st, w.partials, pdl};
     const int every = check_every();
     int32_t launched = 0;
     for (;;) {
@@ -383,10 +403,11 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
         const int32_t batch = std::min<int32_t>(every, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
-            cg_alpha_kernel<<<1, kThreads, 0, s>>>(w.partials, P, w.st);
-            update<<<Gu, kThreads, 0, s>>>(n, x, r, p, q, w.partials, w.st);
-            cg_beta_kernel<<<1, kThreads, 0, s>>>(w.partials, (int64_t)Gu, w.st);
-            pupdate<<<Gp, kThreads, 0, s>>>(n, r, p, w.st);
+            launch_kernel(pdl, cg_alpha_kernel, 1, kThreads, 0, s, (const double*)w.partials, P, w.st);
+            launch_kernel(pdl, update, Gu, kThreads, 0, s, n, x, r, (const V*)p, (const V*)q, w.partials,
+                          (const CgState*)w.st);
+            launch_kernel(pdl, cg_beta_kernel, 1, kThreads, 0, s, (const double*)w.partials, (int64_t)Gu, w.st);
+            launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, (const V*)r, p, (const CgState*)w.st);
         }
         MSPV_CUDA_TRY(cudaGetLastError());
         launched += batch;

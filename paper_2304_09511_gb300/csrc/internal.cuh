@@ -131,7 +131,32 @@ struct CgState {
 struct DotEpilogue {
     CgState* st;
     double* partials;   // one per CTA of the launch
+    bool pdl = false;   // launch as a programmatic dependent launch (inside the CG loop)
 };
+
+// Programmatic dependent launch. A kernel launched with the programmatic-serialisation
+// attribute may be scheduled while the previous kernel of its stream is still running; it
+// waits for that kernel's completion and memory (griddepcontrol.wait) before reading
+// anything. pdl_trigger lets the next such kernel be scheduled early. Both are no-ops in a
+// kernel launched without the attribute. The wait ends when the previous grid completes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);   // errors surface via cudaGetLastError
+}
 
 // COO per-window carry record: rows that cross a window boundary leave partial sums.
 struct CooCarry {

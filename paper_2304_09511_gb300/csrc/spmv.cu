@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
     constexpr int RPT = DiaVec<VT, T>::RPT;
+    pdl_wait();
+    pdl_trigger();
     if (ep.st && ep.st->done) return;   // uniform: CG already finished
     __shared__ int32_t s_off[kDiaSmemDiags];
     for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
@@ -211,6 +213,8 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
     const VT* __restrict__ av, const float* __restrict__ x, float* __restrict__ y, DotEpilogue ep) {
     constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 values) or 8 (BF16 values)
     constexpr int NW = RPT / 4 + 1;               // windows covering RPT values at any shift
+    pdl_wait();
+    pdl_trigger();
     if (ep.st && ep.st->done) return;
     __shared__ int32_t s_off[kDiaSmemDiags];
     for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
@@ -294,6 +298,8 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, int32_t long_len,
     DotEpilogue ep) {
+    pdl_wait();
+    pdl_trigger();
     if (ep.st && ep.st->done) return;
     const int64_t gt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int64_t row = gt / V;
@@ -320,6 +326,8 @@ template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_csr_long_kernel(
     const int32_t* __restrict__ long_rows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
+    pdl_wait();
+    pdl_trigger();
     if (ep.st && ep.st->done) return;
     __shared__ T s_red[kThreads];
     const int32_t row = long_rows[blockIdx.x];
@@ -488,6 +496,8 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
     const int32_t* __restrict__ irp, const int32_t* __restrict__ aj, const VT* __restrict__ av,
     const int32_t* __restrict__ row_block, const T* __restrict__ x, T* __restrict__ y,
     DotEpilogue ep) {
+    pdl_wait();
+    pdl_trigger();
     if (ep.st && ep.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* a_s = reinterpret_cast<T*>(smem_raw);
@@ -545,6 +555,8 @@ template <typename VT, typename T, int WCAP, int NT>
 __global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj, const VT* __restrict__ av,
     const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
+    pdl_wait();
+    pdl_trigger();
     if (ep.st && ep.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -636,6 +648,8 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
     CooCarry* __restrict__ carry, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st && st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* a_s = reinterpret_cast<T*>(smem_raw);
@@ -721,6 +735,8 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
     int64_t nchunks, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st && st->done) return;
     __shared__ int32_t s_rs[kThreads / 32][kCooVecChunk + 1];
     __shared__ int32_t s_row[kThreads / 32][kCooVecChunk];
@@ -798,6 +814,8 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
 template <typename T>
 __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_t nwin,
                                       T* __restrict__ y, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st && st->done) return;
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwin - 1) return;   // the last window cannot continue into another
@@ -849,6 +867,8 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
     int64_t nchunks, const CgState* st) {
+    pdl_wait();
+    pdl_trigger();
     if (st && st->done) return;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -970,6 +990,8 @@ __global__ void fill_zero_kernel(T* __restrict__ y, int64_t n) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dot_alpha_kernel(int64_t n, const T* __restrict__ p,
                                                              const T* __restrict__ q, DotEpilogue ep) {
+    pdl_wait();
+    pdl_trigger();
     if (ep.st->done) return;
     T d = T(0);
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
@@ -1087,11 +1109,11 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     int64_t grid = ((int64_t)A->nrows + strip - 1) / strip;
     if (grid < 1) grid = 1;
     if constexpr (sizeof(T) == 4) {
-        spmv_dia_f32_kernel<VT><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
-                                                                    static_cast<const VT*>(A->av), x, y, ep);
+        launch_kernel(ep.pdl, spmv_dia_f32_kernel<VT>, (unsigned)grid, kThreads, 0, s, A->nrows, A->ndiags,
+                      A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
     } else {
-        spmv_dia_kernel<VT, T><<<(unsigned)grid, kThreads, 0, s>>>(A->nrows, A->ndiags, A->npad, A->doff,
-                                                                   static_cast<const VT*>(A->av), x, y, ep);
+        launch_kernel(ep.pdl, spmv_dia_kernel<VT, T>, (unsigned)grid, kThreads, 0, s, A->nrows, A->ndiags,
+                      A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
     }
 }
 
@@ -1150,21 +1172,21 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         constexpr size_t smem = csr_warp_smem<T, kCsrWarpCap, kCsrWarpThreads>();
         allow_smem<K>(smem);
         const int64_t grid = csr_warp_grid<VT, T>(A->nrows);
-        K<<<(unsigned)grid, kCsrWarpThreads, smem, s>>>(A->nrows, A->irp, A->aj, av, x, y, ep);
+        launch_kernel(ep.pdl, K, (unsigned)grid, kCsrWarpThreads, smem, s, A->nrows, A->irp, A->aj, av, x, y, ep);
         return;
     }
     if (V == 0) {
         allow_smem<spmv_csr_stage_kernel<VT, T>>(csr_smem<T>());
-        spmv_csr_stage_kernel<VT, T><<<(unsigned)A->nblocks, kThreads, csr_smem<T>(), s>>>(
-            A->irp, A->aj, av, A->row_block, x, y, ep);
+        launch_kernel(ep.pdl, spmv_csr_stage_kernel<VT, T>, (unsigned)A->nblocks, kThreads, csr_smem<T>(), s,
+                      A->irp, A->aj, av, A->row_block, x, y, ep);
         return;
     }
     const unsigned grid = blocks_for((int64_t)A->nrows * V);
     const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
 #define MSPV_CSR_CASE(VV)                                                                    \
     case VV:                                                                                 \
-        spmv_csr_vector_kernel<VT, T, VV><<<grid, kThreads, 0, s>>>(A->nrows, A->irp, A->aj, \
-                                                                    av, x, y, long_len, ep); \
+        launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV>, grid, kThreads, 0, s, A->nrows, \
+                      A->irp, A->aj, av, x, y, long_len, ep);                                \
         break;
     switch (V) {
         MSPV_CSR_CASE(1)
@@ -1177,9 +1199,9 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     }
 #undef MSPV_CSR_CASE
     if (A->nlong > 0) {
-        const DotEpilogue lep{ep.st, ep.partials ? ep.partials + grid : nullptr};
-        spmv_csr_long_kernel<VT, T><<<(unsigned)A->nlong, kThreads, 0, s>>>(A->long_rows, A->irp, A->aj, av, x, y,
-                                                                            lep);
+        const DotEpilogue lep{ep.st, ep.partials ? ep.partials + grid : nullptr, ep.pdl};
+        launch_kernel(ep.pdl, spmv_csr_long_kernel<VT, T>, (unsigned)A->nlong, kThreads, 0, s, A->long_rows,
+                      A->irp, A->aj, av, x, y, lep);
     }
 }
 
@@ -1197,16 +1219,21 @@ static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     int64_t nch;
     if (A->coo_kernel == 1) {
         nch = A->nchunks;
-        spmv_coo_vec_kernel<VT, T><<<(unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(
-            A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, ep.st);
+        launch_kernel(ep.pdl, spmv_coo_vec_kernel<VT, T>, (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)),
+                      kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y,
+                      A->carry, nch, (const CgState*)ep.st);
     } else {
         nch = (A->nnz + kCooSegChunk - 1) / kCooSegChunk;
-        spmv_coo_seg_kernel<VT, T><<<(unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, s>>>(
-            A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, ep.st);
+        launch_kernel(ep.pdl, spmv_coo_seg_kernel<VT, T>, (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)),
+                      kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y,
+                      A->carry, nch, (const CgState*)ep.st);
     }
-    if (nch > 1) spmv_coo_fixup_kernel<T><<<blocks_for(nch), kThreads, 0, s>>>(A->carry, nch, y, ep.st);
+    if (nch > 1)
+        launch_kernel(ep.pdl, spmv_coo_fixup_kernel<T>, blocks_for(nch), kThreads, 0, s, (const CooCarry*)A->carry,
+                      nch, y, (const CgState*)ep.st);
     if (ep.st)
-        dot_alpha_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(A->nrows, x, y, ep);
+        launch_kernel(ep.pdl, dot_alpha_kernel<T>, (unsigned)vector_grid(A->nrows), kThreads, 0, s,
+                      (int64_t)A->nrows, x, (const T*)y, ep);
 }
 
 // COO SpMV on raw, row-sorted FP64 device triplets with caller-provided carry records
