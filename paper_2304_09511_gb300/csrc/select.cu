@@ -145,17 +145,18 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
     return z ^ (z >> 31);
 }
 
-// Uniform Glorot value of trained parameter k: (2u - 1) sqrt(6 / (fan_in + fan_out)) with
-// u = (top 24 bits of SplitMix64 output k) / 2^24; biases start at zero.
-__device__ __forceinline__ float init_param(uint64_t seed, int k) {
+// Initial value of parameter `a` (absolute index in the layout, a >= OFF_W1): a weight is
+// (2u - 1) sqrt(6 / (fan_in + fan_out)) with u = (top 24 bits of SplitMix64 output
+// a - OFF_W1) / 2^24 (uniform Glorot); biases start at zero.
+__device__ __forceinline__ float init_param(uint64_t seed, int a) {
     int fan_in, fan_out;
-    if (k < OFF_B1) { fan_in = NF; fan_out = NH; }
-    else if (k < OFF_W2) return 0.0f;
-    else if (k < OFF_B2) { fan_in = NH; fan_out = NH; }
-    else if (k < OFF_W3) return 0.0f;
-    else if (k < OFF_B3) { fan_in = NH; fan_out = NC; }
+    if (a < OFF_B1) { fan_in = NF; fan_out = NH; }
+    else if (a < OFF_W2) return 0.0f;
+    else if (a < OFF_B2) { fan_in = NH; fan_out = NH; }
+    else if (a < OFF_W3) return 0.0f;
+    else if (a < OFF_B3) { fan_in = NH; fan_out = NC; }
     else return 0.0f;
-    const float u = (float)(splitmix64_at(seed, (uint64_t)k) >> 40) * (1.0f / 16777216.0f);
+    const float u = (float)(splitmix64_at(seed, (uint64_t)(a - OFF_W1)) >> 40) * (1.0f / 16777216.0f);
     return (2.0f * u - 1.0f) * sqrtf(6.0f / (float)(fan_in + fan_out));
 }
 
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) selector_train_kernel(const float* _
         S.p[OFF_SD + t] = sd > 1e-6 ? (float)sd : 1.0f;
     }
     for (int k = OFF_W1 + t; k < NPARAM; k += kThreads) {
-        S.p[k] = init_param(seed, k - OFF_W1);
+        S.p[k] = init_param(seed, k);
         S.m[k] = 0.0f;
         S.v[k] = 0.0f;
     }

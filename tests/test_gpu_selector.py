@@ -119,6 +119,19 @@ def _separable(n, seed):
     return X.astype(np.float32), y.astype(np.int32)
 
 
+def test_initial_parameters_match_oracle(mspv):
+    """epochs = 0 returns the standardisation and the SplitMix64 Glorot initialisation."""
+    X, y = _separable(100, 4)
+    p = mspv.selector_train(X, y, epochs=0, lr=1e-3, seed=17).astype(np.float64)
+    want = sel.init_params(17)
+    k = slice(2 * sel.NF, sel.NPARAM)
+    np.testing.assert_allclose(p[k], want[k], rtol=1e-6, atol=1e-7)
+    d = sel.unpack(p)
+    np.testing.assert_allclose(d["mu"], X.astype(np.float64).mean(0), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(d["sd"], X.astype(np.float64).std(0), rtol=1e-6)
+    assert np.all(d["b1"] == 0) and np.all(d["b2"] == 0) and np.all(d["b3"] == 0)
+
+
 def test_one_adam_step_matches_oracle(mspv):
     """After one minibatch step every parameter moves by lr * g / (|g| + eps) on both sides.
     Where |g| is within FP32 rounding of zero its sign is not unique: there only the step's
