@@ -66,6 +66,21 @@ def dist_env():
     return world, rank, local
 
 
+def shard(count: int, world: int, rank: int) -> range:
+    """Independent units (e.g. the selector's matrices) dealt round-robin to the ranks."""
+    return range(rank, count, world)
+
+
+def gather_records(rec: list, world: int, key: str = "seed") -> list:
+    """Every rank's records, concatenated and ordered by `key` (on every rank)."""
+    if world <= 1:
+        return sorted(rec, key=lambda x: x[key])
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, rec)
+    return sorted((x for part in parts for x in part), key=lambda x: x[key])
+
+
 def max_over_ranks(value: float, world: int) -> float:
     if world <= 1:
         return value
@@ -360,7 +375,7 @@ def run_selector(args, world, rank, local):
     FMT = ("coo", "csr", "dia")
     rec = []
     t_label = time.perf_counter()
-    for seed in range(rank, args.matrices, world):
+    for seed in shard(args.matrices, world, rank):
         fam, n, r, c, v = synth.family_matrix_torch(seed, dev)
         A = mspv.Matrix.from_coo(n, n, r, c, v)
         del r, c, v
@@ -376,12 +391,8 @@ def run_selector(args, world, rank, local):
         rec.append({"seed": seed, "family": fam, "n": n, "nnz": nnz, "features": f.tolist(),
                     "ms": [ms[k] for k in FMT], "best": FMT.index(best), "t_feat": t_feat, "t_tune": t_tune})
     t_label = time.perf_counter() - t_label
-    if world > 1:
-        import torch.distributed as dist
-        allrec = [None] * world
-        dist.all_gather_object(allrec, rec)
-        rec = sorted((x for part in allrec for x in part), key=lambda x: x["seed"])
-        t_label = max_over_ranks(t_label, world)
+    rec = gather_records(rec, world)
+    t_label = max_over_ranks(t_label, world)
     out = None
     if rank == 0:
         X = np.array([x["features"] for x in rec], dtype=np.float32)
@@ -483,6 +494,82 @@ def _selector_stencil_e2e(mspv, torch, dev, params, g):
 
 
 # ---------------------------------------------------------------------------
+# mixed precision on a large stencil: FP64 CG vs iterative refinement
+# ---------------------------------------------------------------------------
+MIXED_METRIC = "CG time-to-1e-10 on the 27-point stencil, FP64 vs FP32/BF16-value refinement"
+
+
+def run_mixed(args, world, rank, local):
+    """FP64 CG against FP64-outer iterative refinement with FP32 or BF16 stored values (inner
+    CG in FP64 arithmetic, and in FP32 arithmetic), CSR and DIA, on the g^3 stencil with
+    b = A 1 from x0 = 0, each to a 1e-10 relative residual; error against x = 1 reported."""
+    import torch
+    import paper_2304_09511_gb300 as mspv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    g = args.mixed_grid
+    n = g ** 3
+    r, c, v = synth.stencil27_torch(g, dev)
+    A = mspv.Matrix.from_coo(n, n, r, c, v)
+    nnz = A.info["nnz"]
+    del r, c, v
+    stream = torch.cuda.current_stream()
+    os.environ["MSPV_CG_CHECK_EVERY"] = "10"
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        xx = torch.zeros(n, dtype=torch.float64, device=dev)
+        fn(xx)
+        xx.zero_()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        res = fn(xx)
+        e0.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(s0.elapsed_time(e0), world)
+        return {"ms": round(ms, 2), "iters": res.iters, "outer": res.outer_iters, "relres": res.relres,
+                "converged": res.converged, "max_abs_err_vs_x1": float((xx - 1.0).abs().max().item())}
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    results = {}
+    for fmt in ("csr", "dia"):
+        M = A.convert(fmt)
+        b = M.spmv(ones)
+        out = {"fp64_cg": timed(lambda xx: M.cg(b, x=xx, tol=1e-10, maxit=20000))}
+        for vt in ("f32", "bf16"):
+            L = A.convert(fmt, vt)
+            out[f"ir_{vt}_values_fp64_inner"] = timed(
+                lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=1e-5, max_outer=30, maxit_inner=20000))
+            out[f"ir_{vt}_values_fp32_inner"] = timed(
+                lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=1e-4, max_outer=30, maxit_inner=20000,
+                                   inner_fp32=True))
+            L.close()
+        M.close()
+        results[fmt] = out
+    clk = clocks.stop()
+    best = min((v["ms"], f, k) for f, o in results.items() for k, v in o.items() if v["converged"])
+    out = {"metric": MIXED_METRIC, "value": best[0], "unit": "ms", "higher_is_better": False,
+           "n_gpus": world, "mode": "mixed", "scaling": "weak", "data": "synthetic",
+           "dtype": "f64 outer; f32/bf16 values", "best": {"format": best[1], "solver": best[2]},
+           "config": {"workload": f"27-point stencil {g}^3 (n={n}, nnz={nnz}), b = A 1, x0 = 0, to 1e-10 "
+                                  "relative residual; CSR and DIA; FP64 CG vs FP64-outer refinement with "
+                                  "FP32 or BF16 stored values", "parallelism": f"replicas x{world}"},
+           "results": results, "clocks": clk}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 def oracle_workload(g):
@@ -565,9 +652,11 @@ def main():
     ap.add_argument("--ref-cg-iters", type=int, default=1,
                     help="CG iterations per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "selector"], default="step",
+    ap.add_argument("--mode", choices=["step", "selector", "mixed"], default="step",
                     help="step: the SpMV + CG step (default); selector: tuner labels, MLP "
-                         "training and held-out regret, then the stencil end to end")
+                         "training and held-out regret, then the stencil end to end; mixed: FP64 "
+                         "CG vs FP32/BF16-value refinement on a large stencil")
+    ap.add_argument("--mixed-grid", type=int, default=192, help="mixed mode: stencil grid")
     ap.add_argument("--matrices", type=int, default=2000, help="selector mode: synthetic matrices")
     ap.add_argument("--tune-reps", type=int, default=10, help="selector mode: timed SpMV per format")
     ap.add_argument("--epochs", type=int, default=300, help="selector mode: training epochs")
@@ -582,6 +671,8 @@ def main():
         out = run_reference(args, world, rank)
     elif args.mode == "selector":
         out = run_selector(args, world, rank, local)
+    elif args.mode == "mixed":
+        out = run_mixed(args, world, rank, local)
     else:
         out = run_mspv(args, world, rank, local)
     if out is not None:
