@@ -41,6 +41,33 @@ NDIAGS = 27
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
 
+# DRAM traffic of one spmv_dia_kernel<double, double> launch without the CG epilogue, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 96^3 stencil; it is scaled
+# to the bench grid by rows (every stream of the kernel grows with n). Reported only while the
+# kernel's source (the DIA section of spmv.cu and its launcher) is the one that was captured.
+DIA_TRAFFIC = {"bytes": 202_055_680, "rows": 96 ** 3,
+               "src_sha256": "f772f0a219e01841b9b034400a323c8919789ac2c877848f9696f42dbc12fe34"}
+
+
+def dia_source_sha() -> str | None:
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_2304_09511_gb300", "csrc", "spmv.cu")).read()
+        a = src.index("// DIA\n// ---")
+        b = src.index("// FP32-arithmetic DIA")
+        c = src.index("static void launch_dia(")
+        d = src.index("\n}\n", c)
+    except (OSError, ValueError):
+        return None
+    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()
+
+
+def dia_traffic(n: int) -> int | None:
+    if dia_source_sha() != DIA_TRAFFIC["src_sha256"]:
+        return None
+    return int(round(DIA_TRAFFIC["bytes"] * n / DIA_TRAFFIC["rows"]))
+
+
 def byte_model(n: int, nnz: int, ndiags: int, vbytes: int = 8) -> dict:
     """Algorithmic bytes of one SpMV per format and of one CG iteration (DIA)."""
     coo = (vbytes + 8) * nnz + 16 * n
@@ -329,7 +356,9 @@ def run_mspv(args, world, rank, local):
                      "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
                      "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz x 2 flop",
                      "executed_fma_frac": round(executed_tf / FP64_PEAK_TFLOPS, 4),
-                     "traffic": None, "flops_per_launch": 2 * nnz, "bytes_per_launch": bm["dia"],
+                     "traffic": dia_traffic(n),
+                     "traffic_source": "ncu dram bytes of one launch on the 96^3 stencil, scaled by rows",
+                     "flops_per_launch": 2 * nnz, "bytes_per_launch": bm["dia"],
                      "hbm": {"achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]}},
         "e2e": {"value": round(e2e_value, 1), "unit": "GB/s", "ms_per_step": round(e2e_ms, 4),

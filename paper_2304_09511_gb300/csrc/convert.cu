@@ -560,6 +560,10 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
             MSPV_TRY(exclusive_scan_i32(M->irp, M->irp, M->nrows, M->irp + M->nrows, s));
             M->csr_vector = choose_csr_vector(M->row_mean, M->row_std, M->row_max);
             M->csr_block = choose_csr_block_kernel();
+            {
+                const char* pf = std::getenv("MSPV_CSR_PREFETCH");   // 0: plain lane-strided loop
+                M->csr_prefetch = !(pf && pf[0] == '0');
+            }
             if (M->csr_vector > 0) MSPV_TRY(build_csr_long_rows(M, s));
             MSPV_TRY(build_csr_row_blocks(M, s));
         }
@@ -614,10 +618,20 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
     return MSPV_OK;
 }
 
+// COO kernel for the longest row: short rows (at most 128 entries) take the run-vector
+// kernel, whose 4 lanes per run gather neighbouring columns together (stencil-like rows);
+// matrices with longer rows take the lane-sequential segment kernel, which keeps every lane
+// busy however the rows are cut. MSPV_COO_KERNEL=vec|seg overrides.
+int32_t choose_coo_kernel(int32_t row_max) {
+    const char* k = std::getenv("MSPV_COO_KERNEL");
+    if (k && std::strcmp(k, "vec") == 0) return 1;
+    if (k && std::strcmp(k, "seg") == 0) return 0;
+    return row_max <= 128 ? 1 : 0;
+}
+
 mspv_status ensure_coo_carry(mspv_matrix* M) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
-    const char* k = std::getenv("MSPV_COO_KERNEL");
-    M->coo_kernel = (k && std::strcmp(k, "vec") == 0) ? 1 : 0;
+    M->coo_kernel = choose_coo_kernel(M->row_max);
     M->nchunks = (M->nnz + kCooVecChunk - 1) / kCooVecChunk;
     MSPV_TRY(dev_alloc_n(&M->carry, M->nchunks > 0 ? M->nchunks : 1));
     M->bytes += (M->nchunks > 0 ? M->nchunks : 1) * (int64_t)sizeof(CooCarry);

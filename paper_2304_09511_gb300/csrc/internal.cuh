@@ -213,6 +213,7 @@ struct mspv_matrix {
     int32_t ndiags = 0, npad = 0;
     int32_t csr_vector = 0;   // 0: staged kernel; 1..32: lanes per row
     int32_t csr_block = 0;    // staged kernel: 0 = warp-private staging, 1 = CTA row blocks
+    int32_t csr_prefetch = 1; // vector kernel: rows of <= 8 V entries load all before the FMAs
     int32_t row_max = 0;
     int32_t row_min = 0;
     double row_mean = 0.0, row_std = 0.0;
@@ -228,7 +229,7 @@ struct mspv_matrix {
 
     mspv::CooCarry* carry = nullptr;   // COO: per-window carries
     int64_t nchunks = 0;               // COO chunks of kCooVecChunk entries
-    int32_t coo_kernel = 0;            // COO: 0 lane-sequential segments, 1 run-vector (MSPV_COO_KERNEL=vec)
+    int32_t coo_kernel = 0;            // COO: 0 lane-sequential segments, 1 run-vector (choose_coo_kernel)
     int32_t* row_block = nullptr;      // CSR: first row of each window, nblocks + 1 entries
     int32_t* long_rows = nullptr;      // CSR vector kernel: rows longer than 32 * csr_vector
     int64_t nlong = 0;
@@ -271,6 +272,7 @@ int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
 mspv_status build_csr_long_rows(mspv_matrix* M, cudaStream_t s);
 int32_t choose_csr_block_kernel();   // MSPV_CSR_KERNEL=block selects CTA row blocks
+int32_t choose_coo_kernel(int32_t row_max);   // 1 run-vector, 0 lane-sequential segments
 
 // cg.cu
 mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,

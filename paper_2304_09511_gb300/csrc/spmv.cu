@@ -293,7 +293,7 @@ __device__ __forceinline__ T convert_value(VT v) {
 // short rows on GB300: a warp instruction still covers 8 rows x 32-byte segments
 // (coalesced enough), while the reduction costs 2 FP64 shuffle-adds per 8 rows. Rows
 // longer than long_len are skipped here and reduced by spmv_csr_long_kernel.
-template <typename VT, typename T, int V>
+template <typename VT, typename T, int V, bool PREFETCH>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, int32_t long_len,
@@ -306,14 +306,41 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     const int lane = threadIdx.x & (V - 1);
     T sum = T(0);
     bool mine = row < nrows;
+    int32_t s = 0, e = 0;
     if (mine) {
-        const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
-        if (e - s > long_len) {
-            mine = false;   // written by the long-row kernel
+        s = __ldg(irp + row);
+        e = __ldg(irp + row + 1);
+        if (e - s > long_len) mine = false;   // written by the long-row kernel
+    }
+    const int cnt = mine ? (e - s - lane + V - 1) / V : 0;   // this lane's entries (may be <= 0)
+    if (PREFETCH) {
+        // rows of at most 8 V entries: issue every load of the lane before the first FMA;
+        // a slot no lane of the warp uses is skipped by a warp-uniform branch
+        const int kmax = __reduce_max_sync(0xffffffffu, cnt > 8 ? 0 : cnt);
+        if (cnt <= 8) {
+            int32_t jj[8];
+            T aa[8], xx[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k < kmax) {
+                    const bool ok = k < cnt;
+                    jj[k] = ok ? __ldcs(aj + s + lane + k * V) : 0;
+                    aa[k] = ok ? convert_value<T>(__ldcs(av + s + lane + k * V)) : T(0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < kmax) xx[k] = (k < cnt) ? __ldg(x + jj[k]) : T(0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < kmax) sum = fma_t(aa[k], xx[k], sum);
         } else {
             for (int32_t j = s + lane; j < e; j += V)
                 sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
         }
+    } else if (mine) {
+        for (int32_t j = s + lane; j < e; j += V)
+            sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
     }
 #pragma unroll
     for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -1183,10 +1210,14 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     }
     const unsigned grid = blocks_for((int64_t)A->nrows * V);
     const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
-#define MSPV_CSR_CASE(VV)                                                                    \
-    case VV:                                                                                 \
-        launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV>, grid, kThreads, 0, s, A->nrows, \
-                      A->irp, A->aj, av, x, y, long_len, ep);                                \
+#define MSPV_CSR_CASE(VV)                                                                        \
+    case VV:                                                                                     \
+        if (A->csr_prefetch)                                                                     \
+            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, true>, grid, kThreads, 0, s,  \
+                          A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                      \
+        else                                                                                     \
+            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, false>, grid, kThreads, 0, s, \
+                          A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                      \
         break;
     switch (V) {
         MSPV_CSR_CASE(1)
