@@ -76,18 +76,38 @@ __device__ __forceinline__ void write_partial_f32(float v, double* partials) {
 }
 
 // Sum of count partials in index order (one CTA; valid in thread 0).
+constexpr int kScalarThreads = 1024;   // threads of the one-CTA scalar kernels
+
+// Sum of `count` per-CTA partials by one CTA of kScalarThreads threads: thread t adds
+// partials t, t + T, t + 2T, ... into four accumulators (four loads in flight), then the
+// warps and the CTA reduce in a fixed order, so a given count always gives the same
+// result. The total is returned in thread 0.
 __device__ __forceinline__ double sum_partials(const double* partials, int64_t count) {
-    __shared__ double s_red[kThreads];
-    double acc = 0.0;
-    for (int64_t b = threadIdx.x; b < count; b += kThreads) acc += partials[b];
-    return block_sum(acc, s_red);
+    __shared__ double s_warp[kScalarThreads / 32];
+    constexpr int64_t T = kScalarThreads;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t b = threadIdx.x;
+    for (; b + 3 * T < count; b += 4 * T) {
+        a0 += partials[b];
+        a1 += partials[b + T];
+        a2 += partials[b + 2 * T];
+        a3 += partials[b + 3 * T];
+    }
+    for (; b < count; b += T) a0 += partials[b];
+    const double v = warp_sum((a0 + a1) + (a2 + a3));
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) t = warp_sum(s_warp[threadIdx.x]);
+    __syncthreads();
+    return t;
 }
 
 // ---------------------------------------------------------------------------
 // scalar kernels (one CTA)
 // ---------------------------------------------------------------------------
 // rho = r.r, ||b||; converged at the start when r is already small enough (or b = 0).
-__global__ void __launch_bounds__(kThreads) cg_start_kernel(const double* __restrict__ prr,
+__global__ void __launch_bounds__(kScalarThreads) cg_start_kernel(const double* __restrict__ prr,
                                                             const double* __restrict__ pbb, int64_t count,
                                                             CgState* st) {
     const double rr = sum_partials(prr, count);
@@ -104,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) cg_start_kernel(const double* __rest
 }
 
 // alpha = rho / p.q, or a breakdown when p.q <= 0 or alpha is not finite.
-__global__ void __launch_bounds__(kThreads) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
+__global__ void __launch_bounds__(kScalarThreads) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
                                                             CgState* st) {
     pdl_wait();
     pdl_trigger();
@@ -114,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) cg_alpha_kernel(const double* __rest
 }
 
 // rho' = r.r; stop when sqrt(rho') <= tol ||b||; beta = rho' / rho; iteration count.
-__global__ void __launch_bounds__(kThreads) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
+__global__ void __launch_bounds__(kScalarThreads) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
                                                            CgState* st) {
     pdl_wait();
     pdl_trigger();
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) ir_residual_kernel(int64_t n, const 
 }
 
 // rho = r.r and ||b|| of the refinement's outer residual.
-__global__ void __launch_bounds__(kThreads) ir_norms_kernel(const double* __restrict__ prr,
+__global__ void __launch_bounds__(kScalarThreads) ir_norms_kernel(const double* __restrict__ prr,
                                                             const double* __restrict__ pbb, int64_t count,
                                                             CgState* st) {
     const double rr = sum_partials(prr, count);
@@ -403,10 +423,10 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
         const int32_t batch = std::min<int32_t>(every, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
-            launch_kernel(pdl, cg_alpha_kernel, 1, kThreads, 0, s, (const double*)w.partials, P, w.st);
+            launch_kernel(pdl, cg_alpha_kernel, 1, kScalarThreads, 0, s, (const double*)w.partials, P, w.st);
             launch_kernel(pdl, update, Gu, kThreads, 0, s, n, x, r, (const V*)p, (const V*)q, w.partials,
                           (const CgState*)w.st);
-            launch_kernel(pdl, cg_beta_kernel, 1, kThreads, 0, s, (const double*)w.partials, (int64_t)Gu, w.st);
+            launch_kernel(pdl, cg_beta_kernel, 1, kScalarThreads, 0, s, (const double*)w.partials, (int64_t)Gu, w.st);
             launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, (const V*)r, p, (const CgState*)w.st);
         }
         MSPV_CUDA_TRY(cudaGetLastError());
@@ -439,7 +459,7 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
 
     MSPV_TRY(launch_spmv(A, x, w.q, s, DotEpilogue{nullptr, nullptr}));
     cg_init_kernel<<<Gi, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.partials + half);
-    cg_start_kernel<<<1, kThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
+    cg_start_kernel<<<1, kScalarThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
@@ -486,7 +506,7 @@ static mspv_status cg_solve_f32(mspv_matrix* A, const float* b32, float* x32, do
     const int64_t half = w.npartials / 2;
     MSPV_TRY(launch_spmv_f32(A, x32, w.qf, s, DotEpilogue{nullptr, nullptr}));
     cgf_init_kernel<<<Gi, kThreads, 0, s>>>(n, b32, w.qf, w.rf, w.pf, w.partials, w.partials + half);
-    cg_start_kernel<<<1, kThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
+    cg_start_kernel<<<1, kScalarThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_TRY(cg_iterate(
         A, x32, w.rf, w.pf, w.qf, maxit, s,
@@ -539,7 +559,7 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
     for (int32_t k = 0;; ++k) {
         MSPV_TRY(launch_spmv(A64, x, q, s, DotEpilogue{nullptr, nullptr}));
         ir_residual_kernel<<<G, kThreads, 0, s>>>(n, b, q, r, A64->cg.partials, A64->cg.partials + half);
-        ir_norms_kernel<<<1, kThreads, 0, s>>>(A64->cg.partials, A64->cg.partials + half, (int64_t)G, ost);
+        ir_norms_kernel<<<1, kScalarThreads, 0, s>>>(A64->cg.partials, A64->cg.partials + half, (int64_t)G, ost);
         MSPV_CUDA_TRY(cudaGetLastError());
         MSPV_CUDA_TRY(cudaMemcpyAsync(host, ost, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));

@@ -560,10 +560,6 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
             MSPV_TRY(exclusive_scan_i32(M->irp, M->irp, M->nrows, M->irp + M->nrows, s));
             M->csr_vector = choose_csr_vector(M->row_mean, M->row_std, M->row_max);
             M->csr_block = choose_csr_block_kernel();
-            {
-                const char* pf = std::getenv("MSPV_CSR_PREFETCH");   // 0: plain lane-strided loop
-                M->csr_prefetch = !(pf && pf[0] == '0');
-            }
             if (M->csr_vector > 0) MSPV_TRY(build_csr_long_rows(M, s));
             MSPV_TRY(build_csr_row_blocks(M, s));
         }

@@ -213,7 +213,6 @@ struct mspv_matrix {
     int32_t ndiags = 0, npad = 0;
     int32_t csr_vector = 0;   // 0: staged kernel; 1..32: lanes per row
     int32_t csr_block = 0;    // staged kernel: 0 = warp-private staging, 1 = CTA row blocks
-    int32_t csr_prefetch = 1; // vector kernel: rows of <= 8 V entries load all before the FMAs
     int32_t row_max = 0;
     int32_t row_min = 0;
     double row_mean = 0.0, row_std = 0.0;

@@ -293,7 +293,7 @@ __device__ __forceinline__ T convert_value(VT v) {
 // short rows on GB300: a warp instruction still covers 8 rows x 32-byte segments
 // (coalesced enough), while the reduction costs 2 FP64 shuffle-adds per 8 rows. Rows
 // longer than long_len are skipped here and reduced by spmv_csr_long_kernel.
-template <typename VT, typename T, int V, bool PREFETCH>
+template <typename VT, typename T, int V>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, int32_t long_len,
@@ -301,51 +301,35 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     pdl_wait();
     pdl_trigger();
     if (ep.st && ep.st->done) return;
-    const int64_t gt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    const int64_t row = gt / V;
+    // One V-lane group per row; inside CG the grid is capped (fewer partials for the scalar
+    // kernels to sum) and the groups stride over the rows.
     const int lane = threadIdx.x & (V - 1);
-    T sum = T(0);
-    bool mine = row < nrows;
-    int32_t s = 0, e = 0;
-    if (mine) {
-        s = __ldg(irp + row);
-        e = __ldg(irp + row + 1);
-        if (e - s > long_len) mine = false;   // written by the long-row kernel
-    }
-    const int cnt = mine ? (e - s - lane + V - 1) / V : 0;   // this lane's entries (may be <= 0)
-    if (PREFETCH) {
-        // rows of at most 8 V entries: issue every load of the lane before the first FMA;
-        // a slot no lane of the warp uses is skipped by a warp-uniform branch
-        const int kmax = __reduce_max_sync(0xffffffffu, cnt > 8 ? 0 : cnt);
-        if (cnt <= 8) {
-            int32_t jj[8];
-            T aa[8], xx[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (k < kmax) {
-                    const bool ok = k < cnt;
-                    jj[k] = ok ? __ldcs(aj + s + lane + k * V) : 0;
-                    aa[k] = ok ? convert_value<T>(__ldcs(av + s + lane + k * V)) : T(0);
-                }
+    const int64_t stride = (int64_t)gridDim.x * (kThreads / V);
+    // the loop bound is the warp's first row, so all 32 lanes run every shuffle together
+    const int64_t warp_row0 = ((int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31)) / V;
+    const int grp = (threadIdx.x & 31) / V;
+    T dot = T(0);
+    for (int64_t base = warp_row0; base < nrows; base += stride) {
+        const int64_t row = base + grp;
+        T sum = T(0);
+        bool mine = row < nrows;
+        if (mine) {
+            const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
+            if (e - s > long_len) {
+                mine = false;   // written by the long-row kernel
+            } else {
+                for (int32_t j = s + lane; j < e; j += V)
+                    sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
             }
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (k < kmax) xx[k] = (k < cnt) ? __ldg(x + jj[k]) : T(0);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (k < kmax) sum = fma_t(aa[k], xx[k], sum);
-        } else {
-            for (int32_t j = s + lane; j < e; j += V)
-                sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
         }
-    } else if (mine) {
-        for (int32_t j = s + lane; j < e; j += V)
-            sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
-    }
 #pragma unroll
-    for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0 && mine) y[row] = sum;
-    if (ep.st) finish_dot((lane == 0 && mine) ? x[row] * sum : T(0), ep);
+        for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0 && mine) {
+            y[row] = sum;
+            if (ep.st) dot = fma_t(x[row], sum, dot);
+        }
+    }
+    if (ep.st) finish_dot(dot, ep);
 }
 
 // One CTA per long row (listed at conversion): strided FMAs, then a CTA reduction.
@@ -1176,9 +1160,17 @@ static int64_t csr_warp_grid(int32_t nrows) {
     return g < 1 ? 1 : g;
 }
 
+// CTAs of the V-lane kernel; with a dot-product epilogue (inside CG) at most two waves of
+// 8 CTAs per SM, each group of V lanes striding over the rows.
+constexpr int64_t kCsrCgGridCap = (int64_t)kNumSMs * 8 * 2;
+static int64_t csr_vector_grid(const mspv_matrix* A, bool capped) {
+    int64_t g = ((int64_t)A->nrows * A->csr_vector + kThreads - 1) / kThreads;
+    if (capped && g > kCsrCgGridCap) g = kCsrCgGridCap;
+    return g < 1 ? 1 : g;
+}
+
 static int64_t csr_grid_for(const mspv_matrix* A) {
-    if (A->csr_vector != 0)
-        return (int64_t)((A->nrows * (int64_t)A->csr_vector + kThreads - 1) / kThreads) + A->nlong;
+    if (A->csr_vector != 0) return csr_vector_grid(A, true) + A->nlong;
     if (A->csr_block) return A->nblocks;
     if (A->value_type == MSPV_F64) return csr_warp_grid<double, double>(A->nrows);
     // FP32/BF16 values run the FP64-arithmetic or FP32-arithmetic instantiation; both
@@ -1208,16 +1200,12 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
                       A->irp, A->aj, av, A->row_block, x, y, ep);
         return;
     }
-    const unsigned grid = blocks_for((int64_t)A->nrows * V);
+    const unsigned grid = (unsigned)csr_vector_grid(A, ep.partials != nullptr);
     const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
-#define MSPV_CSR_CASE(VV)                                                                        \
-    case VV:                                                                                     \
-        if (A->csr_prefetch)                                                                     \
-            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, true>, grid, kThreads, 0, s,  \
-                          A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                      \
-        else                                                                                     \
-            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, false>, grid, kThreads, 0, s, \
-                          A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                      \
+#define MSPV_CSR_CASE(VV)                                                                    \
+    case VV:                                                                                 \
+        launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV>, grid, kThreads, 0, s, A->nrows, \
+                      A->irp, A->aj, av, x, y, long_len, ep);                                \
         break;
     switch (V) {
         MSPV_CSR_CASE(1)
