@@ -76,15 +76,23 @@ __device__ __forceinline__ void write_partial_f32(float v, double* partials) {
 }
 
 // Sum of count partials in index order (one CTA; valid in thread 0).
-constexpr int kScalarThreads = 1024;   // threads of the one-CTA scalar kernels
+#define MSPV_SCALAR_LAUNCH(pdl, K, count, s, ...)                                              \
+    ((count) > kScalarWideFrom ? launch_kernel(pdl, K<kScalarWide>, 1, kScalarWide, 0, s, __VA_ARGS__) \
+                               : launch_kernel(pdl, K<kThreads>, 1, kThreads, 0, s, __VA_ARGS__))
 
-// Sum of `count` per-CTA partials by one CTA of kScalarThreads threads: thread t adds
-// partials t, t + T, t + 2T, ... into four accumulators (four loads in flight), then the
-// warps and the CTA reduce in a fixed order, so a given count always gives the same
-// result. The total is returned in thread 0.
+// One-CTA scalar kernels run 256 threads, or 1024 when there are more than 16,384 partials
+// to sum (large CSR/DIA grids); the partial count decides, so results stay deterministic.
+constexpr int kScalarWide = 1024;
+constexpr int64_t kScalarWideFrom = 16384;
+
+// Sum of `count` per-CTA partials by one CTA of NT threads: thread t adds partials t, t + NT,
+// t + 2 NT, ... into four accumulators (four loads in flight), then the warps and the CTA
+// reduce in a fixed order, so a given count always gives the same result. The total is
+// returned in thread 0.
+template <int NT>
 __device__ __forceinline__ double sum_partials(const double* partials, int64_t count) {
-    __shared__ double s_warp[kScalarThreads / 32];
-    constexpr int64_t T = kScalarThreads;
+    __shared__ double s_warp[NT / 32];
+    constexpr int64_t T = NT;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int64_t b = threadIdx.x;
     for (; b + 3 * T < count; b += 4 * T) {
@@ -98,7 +106,7 @@ __device__ __forceinline__ double sum_partials(const double* partials, int64_t c
     if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x < 32) t = warp_sum(s_warp[threadIdx.x]);
+    if (threadIdx.x < 32) t = warp_sum(threadIdx.x < NT / 32 ? s_warp[threadIdx.x] : 0.0);
     __syncthreads();
     return t;
 }
@@ -107,11 +115,12 @@ __device__ __forceinline__ double sum_partials(const double* partials, int64_t c
 // scalar kernels (one CTA)
 // ---------------------------------------------------------------------------
 // rho = r.r, ||b||; converged at the start when r is already small enough (or b = 0).
-__global__ void __launch_bounds__(kScalarThreads) cg_start_kernel(const double* __restrict__ prr,
+template <int NT>
+__global__ void __launch_bounds__(NT) cg_start_kernel(const double* __restrict__ prr,
                                                             const double* __restrict__ pbb, int64_t count,
                                                             CgState* st) {
-    const double rr = sum_partials(prr, count);
-    const double bb = sum_partials(pbb, count);
+    const double rr = sum_partials<NT>(prr, count);
+    const double bb = sum_partials<NT>(pbb, count);
     if (threadIdx.x == 0) {
         st->rho = rr;
         st->bnorm = sqrt(bb);
@@ -124,22 +133,24 @@ __global__ void __launch_bounds__(kScalarThreads) cg_start_kernel(const double* 
 }
 
 // alpha = rho / p.q, or a breakdown when p.q <= 0 or alpha is not finite.
-__global__ void __launch_bounds__(kScalarThreads) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
+template <int NT>
+__global__ void __launch_bounds__(NT) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
                                                             CgState* st) {
     pdl_wait();
     pdl_trigger();
     if (st->done) return;
-    const double pq = sum_partials(partials, count);
+    const double pq = sum_partials<NT>(partials, count);
     if (threadIdx.x == 0) finish_alpha(st, pq);
 }
 
 // rho' = r.r; stop when sqrt(rho') <= tol ||b||; beta = rho' / rho; iteration count.
-__global__ void __launch_bounds__(kScalarThreads) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
+template <int NT>
+__global__ void __launch_bounds__(NT) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
                                                            CgState* st) {
     pdl_wait();
     pdl_trigger();
     if (st->done) return;
-    const double rr = sum_partials(partials, count);
+    const double rr = sum_partials<NT>(partials, count);
     if (threadIdx.x == 0) {
         st->iters += 1;
         if (sqrt(rr) <= st->tol * st->bnorm) {
@@ -225,11 +236,12 @@ __global__ void __launch_bounds__(kThreads) ir_residual_kernel(int64_t n, const 
 }
 
 // rho = r.r and ||b|| of the refinement's outer residual.
-__global__ void __launch_bounds__(kScalarThreads) ir_norms_kernel(const double* __restrict__ prr,
+template <int NT>
+__global__ void __launch_bounds__(NT) ir_norms_kernel(const double* __restrict__ prr,
                                                             const double* __restrict__ pbb, int64_t count,
                                                             CgState* st) {
-    const double rr = sum_partials(prr, count);
-    const double bb = sum_partials(pbb, count);
+    const double rr = sum_partials<NT>(prr, count);
+    const double bb = sum_partials<NT>(pbb, count);
     if (threadIdx.x == 0) {
         st->rho = rr;
         st->bnorm = sqrt(bb);
@@ -423,10 +435,10 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
         const int32_t batch = std::min<int32_t>(every, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
-            launch_kernel(pdl, cg_alpha_kernel, 1, kScalarThreads, 0, s, (const double*)w.partials, P, w.st);
+            MSPV_SCALAR_LAUNCH(pdl, cg_alpha_kernel, P, s, (const double*)w.partials, P, w.st);
             launch_kernel(pdl, update, Gu, kThreads, 0, s, n, x, r, (const V*)p, (const V*)q, w.partials,
                           (const CgState*)w.st);
-            launch_kernel(pdl, cg_beta_kernel, 1, kScalarThreads, 0, s, (const double*)w.partials, (int64_t)Gu, w.st);
+            MSPV_SCALAR_LAUNCH(pdl, cg_beta_kernel, (int64_t)Gu, s, (const double*)w.partials, (int64_t)Gu, w.st);
             launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, (const V*)r, p, (const CgState*)w.st);
         }
         MSPV_CUDA_TRY(cudaGetLastError());
@@ -459,7 +471,8 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
 
     MSPV_TRY(launch_spmv(A, x, w.q, s, DotEpilogue{nullptr, nullptr}));
     cg_init_kernel<<<Gi, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.partials + half);
-    cg_start_kernel<<<1, kScalarThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
+    MSPV_SCALAR_LAUNCH(false, cg_start_kernel, (int64_t)Gi, s, (const double*)w.partials,
+                       (const double*)(w.partials + half), (int64_t)Gi, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
@@ -506,7 +519,8 @@ static mspv_status cg_solve_f32(mspv_matrix* A, const float* b32, float* x32, do
     const int64_t half = w.npartials / 2;
     MSPV_TRY(launch_spmv_f32(A, x32, w.qf, s, DotEpilogue{nullptr, nullptr}));
     cgf_init_kernel<<<Gi, kThreads, 0, s>>>(n, b32, w.qf, w.rf, w.pf, w.partials, w.partials + half);
-    cg_start_kernel<<<1, kScalarThreads, 0, s>>>(w.partials, w.partials + half, (int64_t)Gi, w.st);
+    MSPV_SCALAR_LAUNCH(false, cg_start_kernel, (int64_t)Gi, s, (const double*)w.partials,
+                       (const double*)(w.partials + half), (int64_t)Gi, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_TRY(cg_iterate(
         A, x32, w.rf, w.pf, w.qf, maxit, s,
@@ -559,7 +573,8 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
     for (int32_t k = 0;; ++k) {
         MSPV_TRY(launch_spmv(A64, x, q, s, DotEpilogue{nullptr, nullptr}));
         ir_residual_kernel<<<G, kThreads, 0, s>>>(n, b, q, r, A64->cg.partials, A64->cg.partials + half);
-        ir_norms_kernel<<<1, kScalarThreads, 0, s>>>(A64->cg.partials, A64->cg.partials + half, (int64_t)G, ost);
+        MSPV_SCALAR_LAUNCH(false, ir_norms_kernel, (int64_t)G, s, (const double*)A64->cg.partials,
+                           (const double*)(A64->cg.partials + half), (int64_t)G, ost);
         MSPV_CUDA_TRY(cudaGetLastError());
         MSPV_CUDA_TRY(cudaMemcpyAsync(host, ost, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));

@@ -293,7 +293,7 @@ __device__ __forceinline__ T convert_value(VT v) {
 // short rows on GB300: a warp instruction still covers 8 rows x 32-byte segments
 // (coalesced enough), while the reduction costs 2 FP64 shuffle-adds per 8 rows. Rows
 // longer than long_len are skipped here and reduced by spmv_csr_long_kernel.
-template <typename VT, typename T, int V>
+template <typename VT, typename T, int V, bool STRIDE>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, int32_t long_len,
@@ -301,13 +301,13 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     pdl_wait();
     pdl_trigger();
     if (ep.st && ep.st->done) return;
-    // One V-lane group per row; inside CG the grid is capped (fewer partials for the scalar
-    // kernels to sum) and the groups stride over the rows.
+    // One V-lane group per row. Inside CG (STRIDE) the grid is capped, so the scalar kernels
+    // have fewer partials to sum, and the groups stride over the rows; the loop bound is the
+    // warp's first row, so all 32 lanes run every shuffle together.
     const int lane = threadIdx.x & (V - 1);
-    const int64_t stride = (int64_t)gridDim.x * (kThreads / V);
-    // the loop bound is the warp's first row, so all 32 lanes run every shuffle together
-    const int64_t warp_row0 = ((int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31)) / V;
     const int grp = (threadIdx.x & 31) / V;
+    const int64_t warp_row0 = ((int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31)) / V;
+    const int64_t stride = STRIDE ? (int64_t)gridDim.x * (kThreads / V) : 0;
     T dot = T(0);
     for (int64_t base = warp_row0; base < nrows; base += stride) {
         const int64_t row = base + grp;
@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
             y[row] = sum;
             if (ep.st) dot = fma_t(x[row], sum, dot);
         }
+        if (!STRIDE) break;
     }
     if (ep.st) finish_dot(dot, ep);
 }
@@ -1200,12 +1201,17 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
                       A->irp, A->aj, av, A->row_block, x, y, ep);
         return;
     }
-    const unsigned grid = (unsigned)csr_vector_grid(A, ep.partials != nullptr);
+    const bool capped = ep.partials != nullptr;
+    const unsigned grid = (unsigned)csr_vector_grid(A, capped);
     const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
-#define MSPV_CSR_CASE(VV)                                                                    \
-    case VV:                                                                                 \
-        launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV>, grid, kThreads, 0, s, A->nrows, \
-                      A->irp, A->aj, av, x, y, long_len, ep);                                \
+#define MSPV_CSR_CASE(VV)                                                                      \
+    case VV:                                                                                   \
+        if (capped)                                                                            \
+            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, true>, grid, kThreads, 0, s, \
+                          A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                    \
+        else                                                                                   \
+            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, false>, grid, kThreads, 0, s, \
+                          A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                    \
         break;
     switch (V) {
         MSPV_CSR_CASE(1)
