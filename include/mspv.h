@@ -195,7 +195,7 @@ MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t ncols, int64_t
  * can be chosen without building and timing all three.
  */
 #define MSPV_NUM_FEATURES 10
-#define MSPV_SELECTOR_PARAMS 5079
+#define MSPV_SELECTOR_PARAMS 5099
 
 /*
  * The sparsity features of A's stored structure, rounded to FP32, into HOST out[10]:
@@ -225,13 +225,15 @@ MSPV_API mspv_status mspv_tune_format(mspv_matrix_t A, int32_t reps, void* strea
  * Trains the selector MLP (10 -> 64 -> 64 -> 3, ReLU, softmax cross-entropy; class k is
  * mspv_format k) in one CTA on HOST features X[N * 10] (row-major, as mspv_features writes
  * them) and HOST labels y[N] in {0, 1, 2}. Features are standardised by the training set's
- * mean and population standard deviation (1 where that is below 1e-6). Weights start as
+ * mean and population standard deviation (1 where that is below 1e-6), and their minimum and
+ * maximum are kept: at prediction every feature is first clamped to that training range, so a
+ * matrix beyond the training set (e.g. larger) is judged like the most extreme ones seen. Weights start as
  * uniform Glorot values drawn from SplitMix64 output k (seed `seed`) for trained parameter k
  * in layout order, biases at 0. Each epoch runs Adam (Kingma & Ba 2015: beta1 0.9, beta2
  * 0.999, eps 1e-8, step size lr) over minibatches of 64 consecutive samples in index order
  * (the last one may be shorter), each gradient the mean over its minibatch. Writes
  * MSPV_SELECTOR_PARAMS floats to HOST params in the layout
- *   mu[10] sd[10] W1[64][10] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]   (W[out][in]).
+ *   mu[10] sd[10] lo[10] hi[10] W1[64][10] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]   (W[out][in]).
  * Deterministic (fixed summation order). EINVAL for N < 1, epochs < 0, lr <= 0 or a label
  * outside {0, 1, 2}. Synchronous.
  */
@@ -241,7 +243,8 @@ MSPV_API mspv_status mspv_selector_train(const float* X, const int32_t* y, int32
 
 /*
  * Predicted class for each row of HOST features X[N * 10] under HOST params (the layout
- * above): arg max of the logits, the lowest class on ties; into HOST out[N]. N >= 0.
+ * above): features clamped to [lo, hi], standardised, arg max of the logits (the lowest class
+ * on ties); into HOST out[N]. N >= 0.
  * Synchronous.
  */
 MSPV_API mspv_status mspv_selector_predict(const float* params, const float* X, int32_t N,

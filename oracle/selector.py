@@ -27,10 +27,11 @@ import numpy as np
 
 NF, NH, NC = 10, 64, 3
 BATCH = 64
-# parameter layout: mu[10] sd[10] W1[64][10] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]
-_SHAPES = [("mu", (NF,)), ("sd", (NF,)), ("W1", (NH, NF)), ("b1", (NH,)), ("W2", (NH, NH)),
-           ("b2", (NH,)), ("W3", (NC, NH)), ("b3", (NC,))]
+# parameter layout: mu[10] sd[10] lo[10] hi[10] W1[64][10] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]
+_SHAPES = [("mu", (NF,)), ("sd", (NF,)), ("lo", (NF,)), ("hi", (NF,)), ("W1", (NH, NF)), ("b1", (NH,)),
+           ("W2", (NH, NH)), ("b2", (NH,)), ("W3", (NC, NH)), ("b3", (NC,))]
 NPARAM = sum(int(np.prod(s)) for _, s in _SHAPES)
+FIRST_TRAINED = 4 * NF   # mu, sd, lo, hi come from the training data, the rest from Adam
 TRAINED = ("W1", "b1", "W2", "b2", "W3", "b3")
 FORMATS = ("coo", "csr", "dia")
 
@@ -73,12 +74,14 @@ def pack(d: dict) -> np.ndarray:
 
 
 def init_params(seed: int) -> np.ndarray:
-    """mu = 0, sd = 1; trained parameter k (in layout order, counted from W1) is, for a
+    """mu = 0, sd = 1, lo = -inf, hi = +inf; trained parameter k (in layout order, counted from W1) is, for a
     weight, (2u - 1) * sqrt(6 / (fan_in + fan_out)) with u = (top 24 bits of SplitMix64
     output k) / 2^24; biases are 0."""
     d = {name: np.zeros(shape) for name, shape in _SHAPES}
     d["sd"][:] = 1.0
-    ntrain = NPARAM - 2 * NF
+    d["lo"][:] = -np.inf
+    d["hi"][:] = np.inf
+    ntrain = NPARAM - FIRST_TRAINED
     u = np.array([(z >> 40) / float(1 << 24) for z in splitmix64(seed, ntrain)])
     k = 0
     for name in TRAINED:
@@ -96,8 +99,9 @@ def init_params(seed: int) -> np.ndarray:
 # network
 # ---------------------------------------------------------------------------
 def standardise(p: np.ndarray, X) -> np.ndarray:
+    """Clamp each feature to the training range [lo, hi], then standardise."""
     d = unpack(p)
-    return (np.asarray(X, dtype=np.float64) - d["mu"]) / d["sd"]
+    return (np.clip(np.asarray(X, dtype=np.float64), d["lo"], d["hi"]) - d["mu"]) / d["sd"]
 
 
 def forward(p: np.ndarray, Xs: np.ndarray):
@@ -122,7 +126,7 @@ def loss(p: np.ndarray, Xs: np.ndarray, y: np.ndarray) -> float:
 
 
 def gradient(p: np.ndarray, Xs: np.ndarray, y: np.ndarray) -> np.ndarray:
-    """d loss / d p by back-propagation (zero for mu and sd, which are not trained)."""
+    """d loss / d p by back-propagation (zero for mu, sd, lo and hi, which are not trained)."""
     d = unpack(p)
     Z, H1, H2 = forward(p, Xs)
     B = len(y)
@@ -152,8 +156,9 @@ def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def train(X, y, epochs: int, lr: float, seed: int) -> np.ndarray:
     """Standardise by the training set's mean and population standard deviation (1 where it
-    is below 1e-6), initialise from `seed`, then for each epoch take Adam steps over
-    minibatches of 64 consecutive samples in index order."""
+    is below 1e-6), keep its per-feature minimum and maximum (the clamping range used at
+    prediction), initialise from `seed`, then for each epoch take Adam steps over minibatches
+    of 64 consecutive samples in index order."""
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.int64)
     p = init_params(seed)
@@ -161,9 +166,11 @@ def train(X, y, epochs: int, lr: float, seed: int) -> np.ndarray:
     d["mu"][:] = X.mean(axis=0)
     sd = X.std(axis=0)
     d["sd"][:] = np.where(sd > 1e-6, sd, 1.0)
+    d["lo"][:] = X.min(axis=0)
+    d["hi"][:] = X.max(axis=0)
     Xs = standardise(p, X)
     trained = np.zeros(NPARAM, dtype=bool)
-    trained[2 * NF:] = True
+    trained[FIRST_TRAINED:] = True
     m = np.zeros(NPARAM)
     v = np.zeros(NPARAM)
     t = 0

@@ -61,7 +61,7 @@ SIGNATURES = {
 }
 
 NUM_FEATURES = 10
-SELECTOR_PARAMS = 5079
+SELECTOR_PARAMS = 5099
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:

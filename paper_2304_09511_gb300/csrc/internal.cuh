@@ -283,7 +283,7 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
 
 // select.cu: format selection features, run-first tuner, MLP selector
 constexpr int kSelectorFeatures = 10;
-constexpr int kSelectorParams = 5079;   // mu, sd, W1, b1, W2, b2, W3, b3
+constexpr int kSelectorParams = 5099;   // mu, sd, lo, hi, W1, b1, W2, b2, W3, b3
 mspv_status compute_features(const mspv_matrix* A, float* out, cudaStream_t s, int64_t* ndiags = nullptr);
 mspv_status select_format(const mspv_matrix* A, const float* params, cudaStream_t s, int32_t* best);
 mspv_status tune_formats(const mspv_matrix* A, int32_t reps, cudaStream_t s, double* ms, int32_t* best);

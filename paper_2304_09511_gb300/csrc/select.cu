@@ -129,11 +129,12 @@ mspv_status compute_features(const mspv_matrix* A, float* out, cudaStream_t s, i
 // MLP 10 -> 64 -> 64 -> 3
 // ---------------------------------------------------------------------------
 constexpr int NF = kSelectorFeatures, NH = 64, NC = 3, NB = 64;
-constexpr int OFF_MU = 0, OFF_SD = NF, OFF_W1 = 2 * NF, OFF_B1 = OFF_W1 + NH * NF, OFF_W2 = OFF_B1 + NH,
+constexpr int OFF_MU = 0, OFF_SD = NF, OFF_LO = 2 * NF, OFF_HI = 3 * NF, OFF_W1 = 4 * NF,
+              OFF_B1 = OFF_W1 + NH * NF, OFF_W2 = OFF_B1 + NH,
               OFF_B2 = OFF_W2 + NH * NH, OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NC * NH,
               NPARAM = OFF_B3 + NC;
 static_assert(NPARAM == kSelectorParams, "parameter layout");
-constexpr int NTRAIN = NPARAM - OFF_W1;   // trained parameters (everything after mu, sd)
+constexpr int NTRAIN = NPARAM - OFF_W1;   // trained parameters (everything after mu, sd, lo, hi)
 
 // Output k (0-based) of SplitMix64 seeded with `seed` (Steele, Lea, Flood, "Fast splittable
 // pseudorandom number generators", OOPSLA 2014): the state advances by the golden gamma
@@ -189,8 +190,15 @@ __global__ void __launch_bounds__(kThreads) selector_train_kernel(const float* _
             sq += d * d;
         }
         const double sd = sqrt(sq / (N > 0 ? N : 1));
+        float lo = X[t], hi = X[t];
+        for (int i = 1; i < N; ++i) {
+            lo = fminf(lo, X[(int64_t)i * NF + t]);
+            hi = fmaxf(hi, X[(int64_t)i * NF + t]);
+        }
         S.p[OFF_MU + t] = (float)mu;
         S.p[OFF_SD + t] = sd > 1e-6 ? (float)sd : 1.0f;
+        S.p[OFF_LO + t] = lo;
+        S.p[OFF_HI + t] = hi;
     }
     for (int k = OFF_W1 + t; k < NPARAM; k += kThreads) {
         S.p[k] = init_param(seed, k);
@@ -322,7 +330,10 @@ __global__ void selector_predict_kernel(const float* __restrict__ params, const 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float xb[NF], h1[NH];
-    for (int f = 0; f < NF; ++f) xb[f] = (X[i * NF + f] - p[OFF_MU + f]) / p[OFF_SD + f];
+    // features outside the training range are clamped to it: a matrix larger (or more
+    // skewed) than any training matrix is judged like the most extreme ones seen
+    for (int f = 0; f < NF; ++f)
+        xb[f] = (fminf(fmaxf(X[i * NF + f], p[OFF_LO + f]), p[OFF_HI + f]) - p[OFF_MU + f]) / p[OFF_SD + f];
     for (int j = 0; j < NH; ++j) {
         float a = p[OFF_B1 + j];
         for (int f = 0; f < NF; ++f) a = fmaf(p[OFF_W1 + j * NF + f], xb[f], a);

@@ -124,11 +124,13 @@ def test_initial_parameters_match_oracle(mspv):
     X, y = _separable(100, 4)
     p = mspv.selector_train(X, y, epochs=0, lr=1e-3, seed=17).astype(np.float64)
     want = sel.init_params(17)
-    k = slice(2 * sel.NF, sel.NPARAM)
+    k = slice(sel.FIRST_TRAINED, sel.NPARAM)
     np.testing.assert_allclose(p[k], want[k], rtol=1e-6, atol=1e-7)
     d = sel.unpack(p)
     np.testing.assert_allclose(d["mu"], X.astype(np.float64).mean(0), rtol=1e-6, atol=1e-6)
     np.testing.assert_allclose(d["sd"], X.astype(np.float64).std(0), rtol=1e-6)
+    assert np.array_equal(d["lo"], X.min(0).astype(np.float64))
+    assert np.array_equal(d["hi"], X.max(0).astype(np.float64))
     assert np.all(d["b1"] == 0) and np.all(d["b2"] == 0) and np.all(d["b3"] == 0)
 
 
@@ -149,7 +151,7 @@ def test_one_adam_step_matches_oracle(mspv):
     sel.unpack(p0)["sd"][:] = dw["sd"]
     g = sel.gradient(p0, sel.standardise(p0, X.astype(np.float64)), y)
     init = sel.init_params(3)
-    k = slice(2 * sel.NF, sel.NPARAM)
+    k = slice(sel.FIRST_TRAINED, sel.NPARAM)
     diff = np.abs(p[k].astype(np.float64) - want[k])
     tight = diff <= 1e-6 + 1e-5 * np.abs(want[k])
     ambiguous = np.abs(g[k]) <= 1e-3 * np.max(np.abs(g[k]))
@@ -186,3 +188,8 @@ def test_predict_matches_oracle_where_the_margin_is_unique(mspv):
     np.testing.assert_array_equal(got[clear], np.argmax(Z, axis=1)[clear])
     assert np.all((got >= 0) & (got <= 2))
     assert len(mspv.selector_predict(p, np.zeros((0, sel.NF), np.float32))) == 0
+    # features beyond the training range predict as their clamped values
+    d = sel.unpack(p.astype(np.float64))
+    far = Xq * 50.0
+    clamped = np.clip(far, d["lo"], d["hi"]).astype(np.float32)
+    np.testing.assert_array_equal(mspv.selector_predict(p, far), mspv.selector_predict(p, clamped))

@@ -152,9 +152,9 @@ def test_gradient_matches_central_differences():
     X = rng.normal(size=(7, sel.NF))
     y = rng.integers(0, 3, 7)
     g = sel.gradient(p, X, y)
-    assert np.all(g[: 2 * sel.NF] == 0)
-    idx = np.concatenate([rng.choice(np.arange(2 * sel.NF, sel.NPARAM), 150, replace=False),
-                          [sel.NPARAM - 1, sel.NPARAM - 4, 2 * sel.NF]])
+    assert np.all(g[: sel.FIRST_TRAINED] == 0)
+    idx = np.concatenate([rng.choice(np.arange(sel.FIRST_TRAINED, sel.NPARAM), 150, replace=False),
+                          [sel.NPARAM - 1, sel.NPARAM - 4, sel.FIRST_TRAINED]])
     h = 1e-6
     for k in idx:
         e = np.zeros(sel.NPARAM)
@@ -189,6 +189,21 @@ def test_training_separates_a_separable_problem():
     assert sel.loss(p, Xs, y) < 0.5 * sel.loss(p0, sel.standardise(p0, X), y)
     assert np.mean(sel.predict(p, X) == y) >= 0.97
     np.testing.assert_allclose(sel.unpack(p)["mu"], X.mean(0))
+
+
+def test_features_are_clamped_to_the_training_range():
+    """Prediction clamps each feature to [lo, hi] of the training set before standardising;
+    inside the range nothing changes."""
+    rng = np.random.default_rng(12)
+    X = rng.normal(size=(200, sel.NF)) * 3
+    y = rng.integers(0, 3, 200)
+    p = sel.train(X, y, epochs=2, lr=1e-2, seed=4)
+    d = sel.unpack(p)
+    assert np.array_equal(d["lo"], X.min(0)) and np.array_equal(d["hi"], X.max(0))
+    np.testing.assert_array_equal(sel.standardise(p, X), (X - d["mu"]) / d["sd"])
+    far = X * 40.0 + 100.0
+    np.testing.assert_array_equal(sel.logits(p, far), sel.logits(p, np.clip(far, d["lo"], d["hi"])))
+    assert np.all(np.abs(sel.standardise(p, far)) <= np.abs((np.stack([d["lo"], d["hi"]]) - d["mu"]) / d["sd"]).max(0))
 
 
 def test_regret_definition():
