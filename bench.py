@@ -382,9 +382,12 @@ SELECTOR_METRIC = "format-selector regret on held-out matrices vs the run-first 
 def _regret(ms: np.ndarray, picks: np.ndarray) -> dict:
     best = ms.min(axis=1)
     chosen = ms[np.arange(len(picks)), picks]
+    slow = chosen / best
     return {"regret": round(float(chosen.sum() / best.sum() - 1.0), 5),
-            "mean_slowdown": round(float(np.mean(chosen / best)), 5),
-            "max_slowdown": round(float(np.max(chosen / best)), 4),
+            "geomean_slowdown": round(float(np.exp(np.mean(np.log(slow)))), 5),
+            "mean_slowdown": round(float(np.mean(slow)), 5),
+            "max_slowdown": round(float(np.max(slow)), 4),
+            "within_10pct": round(float(np.mean(slow <= 1.10)), 4),
             "exact": round(float(np.mean(chosen == best)), 4)}
 
 
@@ -583,6 +586,13 @@ def run_mixed(args, world, rank, local):
                                    inner_fp32=True))
             L.close()
         M.close()
+        if fmt == "dia":   # inner tolerance of the FP32-arithmetic solver (BF16 values)
+            L = A.convert(fmt, "bf16")
+            for itol in (1e-3, 1e-5, 1e-6):
+                out[f"ir_bf16_values_fp32_inner_tol{itol:g}"] = timed(
+                    lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=itol, max_outer=40, maxit_inner=20000,
+                                       inner_fp32=True))
+            L.close()
         results[fmt] = out
     clk = clocks.stop()
     best = min((v["ms"], f, k) for f, o in results.items() for k, v in o.items() if v["converged"])

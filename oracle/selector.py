@@ -229,13 +229,16 @@ def features(nrows: int, ncols: int, rows, cols) -> np.ndarray:
 def regret(ms: np.ndarray, picks: np.ndarray) -> dict:
     """ms: (N, 3) per-format times (inf where a format was not built); picks: chosen format
     per matrix. Aggregate regret = sum of chosen times / sum of best times - 1; also the
-    mean and maximum per-matrix slowdown and the fraction of picks as fast as the best."""
+    geometric mean, mean and maximum per-matrix slowdown, the share within 10% of the best
+    and the fraction of picks as fast as the best."""
     ms = np.asarray(ms, dtype=np.float64)
     picks = np.asarray(picks)
     best = ms.min(axis=1)
     chosen = ms[np.arange(len(picks)), picks]
     slow = chosen / best
     return {"regret": float(chosen.sum() / best.sum() - 1.0),
+            "geomean_slowdown": float(np.exp(np.mean(np.log(slow)))),
             "mean_slowdown": float(np.mean(slow)),
             "max_slowdown": float(np.max(slow)),
+            "within_10pct": float(np.mean(slow <= 1.10)),
             "exact": float(np.mean(chosen == best))}

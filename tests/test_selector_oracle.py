@@ -212,3 +212,5 @@ def test_regret_definition():
     assert r["regret"] == pytest.approx((1.0 + 1.0 + 2.0) / (1.0 + 0.5 + 2.0) - 1.0)
     assert r["max_slowdown"] == pytest.approx(2.0)
     assert r["exact"] == pytest.approx(2 / 3)
+    assert r["geomean_slowdown"] == pytest.approx(2.0 ** (1 / 3))
+    assert r["within_10pct"] == pytest.approx(2 / 3)
