@@ -187,6 +187,26 @@ MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t ncols, int64_t
                                            void* stream);
 
 /*
+ * y += A x: the accumulating form of mspv_spmv (same arguments, layouts and errors). Rows of A
+ * without entries leave y unchanged. With mspv_split_columns it forms y = A_local x_local +
+ * A_remote x_remote, one call per part.
+ */
+MSPV_API mspv_status mspv_spmv_add(mspv_matrix_t A, const double* x, double* y, void* stream);
+
+/*
+ * Local/remote split (the paper's distributed HPCG, Sec. VI: each process's matrix is split
+ * into a structured local part and an unstructured remote part so that each can take its own
+ * format). For a COO or CSR handle A (nrows x ncols) and 0 <= ncols_local <= ncols, *local
+ * receives the entries with column < ncols_local (nrows x ncols_local) and *remote those with
+ * column >= ncols_local, renumbered from 0 (nrows x (ncols - ncols_local)); both are new
+ * canonical COO handles with A's value type, to be converted and destroyed independently.
+ * A x = local x[0:ncols_local] + remote x[ncols_local:]. EFORMAT for a DIA handle, EINVAL for
+ * ncols_local outside [0, ncols]. Synchronous.
+ */
+MSPV_API mspv_status mspv_split_columns(mspv_matrix_t A, int32_t ncols_local, void* stream,
+                                        mspv_matrix_t* local, mspv_matrix_t* remote);
+
+/*
  * ---- Format selection ----
  * The paper's distributed HPCG chooses each process's format with a run-first auto-tuner
  * (Sec. VI: time every format, keep the fastest), and its related work cites learned

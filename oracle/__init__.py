@@ -167,6 +167,21 @@ def dia_to_coo(A: Matrix) -> Matrix:
     return Matrix(COO, A.nrows, A.ncols, m, ai=r[:m].copy(), aj=c[:m].copy(), av=v[:m].copy())
 
 
+def split_columns(A: Matrix, ncols_local: int):
+    """Local/remote split of a canonical COO matrix (the per-process split of the paper's
+    distributed HPCG, Sec. VI): local = the entries with column < ncols_local, remote = the
+    others with ncols_local subtracted from their columns; entry order is kept, so both
+    stay canonical. A x = local x[:ncols_local] + remote x[ncols_local:]."""
+    if A.fmt != COO:
+        raise ValueError("oracle: split a COO matrix")
+    m = A.aj < ncols_local
+    loc = Matrix(COO, A.nrows, ncols_local, int(m.sum()), ai=A.ai[m].copy(), aj=A.aj[m].copy(),
+                 av=A.av[m].copy())
+    rem = Matrix(COO, A.nrows, A.ncols - ncols_local, int((~m).sum()), ai=A.ai[~m].copy(),
+                 aj=(A.aj[~m] - ncols_local).astype(np.int32), av=A.av[~m].copy())
+    return loc, rem
+
+
 def round_values(vals, value_type: str) -> np.ndarray:
     v = _f64(vals)
     out = np.empty_like(v)

@@ -184,6 +184,21 @@ class Matrix:
         _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
         return CgResult(x, st, it.value, rr.value)
 
+    def spmv_add(self, x, y, stream=None):
+        """y += A x (device float64 tensors); returns y."""
+        _check_vec(x, self.shape[1])
+        _check_vec(y, self.shape[0])
+        _lib.check(load().mspv_spmv_add(self._h, x.data_ptr(), y.data_ptr(), stream_handle(stream)))
+        return y
+
+    def split_columns(self, ncols_local: int, stream=None):
+        """(local, remote): entries with column < ncols_local, and the rest with columns
+        renumbered from 0; both new COO handles."""
+        lo, re = ctypes.c_void_p(), ctypes.c_void_p()
+        _lib.check(load().mspv_split_columns(self._h, int(ncols_local), stream_handle(stream),
+                                             ctypes.byref(lo), ctypes.byref(re)))
+        return Matrix(lo.value), Matrix(re.value)
+
     def features(self, stream=None) -> np.ndarray:
         """The ten FP32 sparsity features of the stored structure (mspv_features)."""
         out = np.zeros(NUM_FEATURES, dtype=np.float32)

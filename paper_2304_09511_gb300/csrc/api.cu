@@ -262,6 +262,44 @@ MSPV_API mspv_status mspv_export(mspv_matrix_t A, int32_t* idx0, int32_t* idx1, 
     MSPV_GUARD_END
 }
 
+MSPV_API mspv_status mspv_spmv_add(mspv_matrix_t A, const double* x, double* y, void* stream) {
+    MSPV_GUARD_BEGIN
+    if (!A) return set_error(MSPV_EINVAL, "spmv_add: A is NULL");
+    if ((!x && A->ncols > 0) || (!y && A->nrows > 0)) return set_error(MSPV_EINVAL, "spmv_add: NULL vector");
+    if (x == y && A->nrows > 0) return set_error(MSPV_EINVAL, "spmv_add: x and y must not overlap");
+    DotEpilogue ep{nullptr, nullptr};
+    ep.acc = true;
+    return launch_spmv(A, x, y, as_stream(stream), ep);
+    MSPV_GUARD_END
+}
+
+MSPV_API mspv_status mspv_split_columns(mspv_matrix_t A, int32_t ncols_local, void* stream, mspv_matrix_t* local,
+                                        mspv_matrix_t* remote) {
+    MSPV_GUARD_BEGIN
+    if (!local || !remote) return set_error(MSPV_EINVAL, "split_columns: NULL output");
+    *local = nullptr;
+    *remote = nullptr;
+    if (!A) return set_error(MSPV_EINVAL, "split_columns: A is NULL");
+    if (ncols_local < 0 || ncols_local > A->ncols)
+        return set_error(MSPV_EINVAL, "split_columns: ncols_local = %d outside [0, %d]", ncols_local, A->ncols);
+    cudaStream_t s = as_stream(stream);
+    mspv_matrix* L = new mspv_matrix();
+    mspv_matrix* R = new mspv_matrix();
+    L->device = R->device = A->device;
+    const mspv_status st = split_columns(A, ncols_local, s, L, R);
+    if (st != MSPV_OK) {
+        cudaStreamSynchronize(s);
+        mspv_destroy(L);
+        mspv_destroy(R);
+        return st;
+    }
+    *local = L;
+    *remote = R;
+    clear_error();
+    return MSPV_OK;
+    MSPV_GUARD_END
+}
+
 MSPV_API mspv_status mspv_features(mspv_matrix_t A, float* out, void* stream) {
     MSPV_GUARD_BEGIN
     if (!A || !out) return set_error(MSPV_EINVAL, "features: NULL argument");

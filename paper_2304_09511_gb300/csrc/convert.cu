@@ -614,6 +614,106 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
     return MSPV_OK;
 }
 
+// ---------------------------------------------------------------------------
+// column split: local part (columns < c) and remote part (columns >= c, shifted by -c)
+// ---------------------------------------------------------------------------
+__global__ void split_flag_kernel(const int32_t* __restrict__ aj, int64_t nnz, int32_t c, int32_t* __restrict__ flag) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = aj[e] < c ? 1 : 0;
+}
+
+template <typename W>
+__global__ void split_scatter_kernel(const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
+                                     const W* __restrict__ av, const int32_t* __restrict__ pos, int64_t nnz,
+                                     int32_t c, int32_t* __restrict__ li, int32_t* __restrict__ lj,
+                                     W* __restrict__ lv, int32_t* __restrict__ ri, int32_t* __restrict__ rj,
+                                     W* __restrict__ rv) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = aj[e];
+        const int64_t p = pos[e];   // local entries before e
+        if (j < c) {
+            li[p] = ai[e];
+            lj[p] = j;
+            lv[p] = av[e];
+        } else {
+            const int64_t q = e - p;
+            ri[q] = ai[e];
+            rj[q] = j - c;
+            rv[q] = av[e];
+        }
+    }
+}
+
+static mspv_status alloc_coo_part(mspv_matrix* M, int32_t nrows, int32_t ncols, int64_t nnz, int32_t vt) {
+    M->format = MSPV_COO;
+    M->value_type = vt;
+    M->nrows = nrows;
+    M->ncols = ncols;
+    M->nnz = nnz;
+    const size_t vs = value_size(vt);
+    MSPV_TRY(dev_alloc_n(&M->ai, nnz > 0 ? nnz : 1));
+    MSPV_TRY(dev_alloc_n(&M->aj, nnz > 0 ? nnz : 1));
+    MSPV_TRY(dev_alloc(&M->av, vs * (size_t)(nnz > 0 ? nnz : 1)));
+    M->av_count = nnz;
+    M->bytes += nnz * (8 + (int64_t)vs);
+    return MSPV_OK;
+}
+
+mspv_status split_columns(const mspv_matrix* A, int32_t c, cudaStream_t s, mspv_matrix* L, mspv_matrix* R) {
+    if (A->format == MSPV_DIA)
+        return set_error(MSPV_EFORMAT, "split: pass a COO or CSR handle");
+    const int64_t nnz = A->nnz;
+    DevBuf rows_tmp, flag, pos, total;
+    const int32_t* src_ai = A->ai;
+    if (A->format == MSPV_CSR) {
+        MSPV_TRY(rows_tmp.alloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
+        if (A->nrows > 0)
+            expand_rows_kernel<<<grid_for(A->nrows), kThreads, 0, s>>>(A->irp, A->nrows, rows_tmp.as<int32_t>());
+        src_ai = rows_tmp.as<int32_t>();
+    }
+    MSPV_TRY(flag.alloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
+    MSPV_TRY(pos.alloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
+    MSPV_TRY(total.alloc(sizeof(int32_t)));
+    MSPV_CUDA_TRY(cudaMemsetAsync(total.ptr, 0, sizeof(int32_t), s));
+    if (nnz > 0) {
+        split_flag_kernel<<<grid_for(nnz), kThreads, 0, s>>>(A->aj, nnz, c, flag.as<int32_t>());
+        MSPV_CUDA_TRY(cudaGetLastError());
+        MSPV_TRY(exclusive_scan_i32(flag.as<int32_t>(), pos.as<int32_t>(), nnz, total.as<int32_t>(), s));
+    }
+    int32_t nloc = 0;
+    MSPV_CUDA_TRY(cudaMemcpyAsync(&nloc, total.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    MSPV_TRY(alloc_coo_part(L, A->nrows, c, nloc, A->value_type));
+    MSPV_TRY(alloc_coo_part(R, A->nrows, A->ncols - c, nnz - nloc, A->value_type));
+    if (nnz > 0) {
+        const unsigned g = grid_for(nnz);
+        const int32_t* pp = pos.as<int32_t>();
+        switch (value_size(A->value_type)) {
+            case 8:
+                split_scatter_kernel<uint64_t><<<g, kThreads, 0, s>>>(
+                    src_ai, A->aj, static_cast<const uint64_t*>(A->av), pp, nnz, c, L->ai, L->aj,
+                    static_cast<uint64_t*>(L->av), R->ai, R->aj, static_cast<uint64_t*>(R->av));
+                break;
+            case 4:
+                split_scatter_kernel<uint32_t><<<g, kThreads, 0, s>>>(
+                    src_ai, A->aj, static_cast<const uint32_t*>(A->av), pp, nnz, c, L->ai, L->aj,
+                    static_cast<uint32_t*>(L->av), R->ai, R->aj, static_cast<uint32_t*>(R->av));
+                break;
+            default:
+                split_scatter_kernel<uint16_t><<<g, kThreads, 0, s>>>(
+                    src_ai, A->aj, static_cast<const uint16_t*>(A->av), pp, nnz, c, L->ai, L->aj,
+                    static_cast<uint16_t*>(L->av), R->ai, R->aj, static_cast<uint16_t*>(R->av));
+        }
+        MSPV_CUDA_TRY(cudaGetLastError());
+    }
+    MSPV_TRY(finish_coo_stats(L, s));
+    MSPV_TRY(ensure_coo_carry(L));
+    MSPV_TRY(finish_coo_stats(R, s));
+    MSPV_TRY(ensure_coo_carry(R));
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    return MSPV_OK;
+}
+
 // COO kernel for the longest row: short rows (at most 128 entries) take the run-vector
 // kernel, whose 4 lanes per run gather neighbouring columns together (stencil-like rows);
 // matrices with longer rows take the lane-sequential segment kernel, which keeps every lane

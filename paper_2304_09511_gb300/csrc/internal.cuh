@@ -132,7 +132,19 @@ struct DotEpilogue {
     CgState* st;
     double* partials;   // one per CTA of the launch
     bool pdl = false;   // launch as a programmatic dependent launch (inside the CG loop)
+    bool acc = false;   // y += A x instead of y = A x (never together with a dot product)
 };
+
+// The one place each SpMV kernel writes a row of y: overwrite, or add (accumulating SpMV).
+template <typename T>
+__device__ __forceinline__ void store_y(T* y, int64_t i, T v, bool acc) {
+    y[i] = acc ? y[i] + v : v;
+}
+// A row without entries: 0 when overwriting, untouched when accumulating.
+template <typename T>
+__device__ __forceinline__ void zero_y(T* y, int64_t i, bool acc) {
+    if (!acc) y[i] = T(0);
+}
 
 // Programmatic dependent launch. A kernel launched with the programmatic-serialisation
 // attribute may be scheduled while the previous kernel of its stream is still running; it
@@ -255,6 +267,9 @@ void free_matrix(mspv_matrix* M);
 double dia_slot_cap(int64_t nnz);
 mspv_status ensure_coo_carry(mspv_matrix* M);
 mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
+// Local part (columns < c) and remote part (columns >= c, renumbered from 0) of a COO/CSR
+// handle, both canonical COO handles with A's value type.
+mspv_status split_columns(const mspv_matrix* A, int32_t c, cudaStream_t s, mspv_matrix* L, mspv_matrix* R);
 
 // spmv.cu
 mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaStream_t s,

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             if (i0 + r < n) {
-                y[i0 + r] = acc[r];
+                store_y(y, i0 + r, acc[r], ep.acc);
                 if (ep.st) d = fma_t(__ldg(x + i0 + r), acc[r], d);
             }
         }
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
             if (i0 + r < n) {
-                y[i0 + r] = acc[r];
+                store_y(y, i0 + r, acc[r], ep.acc);
                 if (ep.st) d = fmaf(__ldg(x + i0 + r), acc[r], d);
             }
     }
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
 #pragma unroll
         for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == 0 && mine) {
-            y[row] = sum;
+            store_y(y, row, sum, ep.acc);
             if (ep.st) dot = fma_t(x[row], sum, dot);
         }
         if (!STRIDE) break;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_long_kernel(
         part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
     const T sum = block_sum_t(part, s_red);
     if (threadIdx.x == 0) {
-        y[row] = sum;
+        store_y(y, row, sum, ep.acc);
         if (ep.st) ep.partials[blockIdx.x] = to_f64_exact(x[row] * sum);
     }
 }
@@ -527,14 +527,14 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
             stage_window(aj, av, x, s, len, a_s, x_s);
             __syncthreads();
             reduce_runs<VT>(a_s, x_s, rs, nr, [&](int i, T sum) {
-                y[rb + i] = sum;
+                store_y(y, rb + i, sum, ep.acc);
                 if (ep.st) dot = fma_t(x[rb + i], sum, dot);
             });
         } else {
             for (int32_t r = rb; r < re; ++r) {   // uniform over the CTA
                 const int32_t a = __ldg(irp + r), b = __ldg(irp + r + 1);
                 if (a == b) {
-                    if (threadIdx.x == 0) y[r] = T(0);
+                    if (threadIdx.x == 0) zero_y(y, r, ep.acc);
                     continue;
                 }
                 T part = T(0);
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
                     part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
                 const T sum = block_sum_t(part, s_red_t);
                 if (threadIdx.x == 0) {
-                    y[r] = sum;
+                    store_y(y, r, sum, ep.acc);
                     if (ep.st) dot = fma_t(x[r], sum, dot);
                 }
             }
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
                 if (lane == q) {
-                    y[row] = part;
+                    store_y(y, row, part, ep.acc);
                     if (ep.st) dot = fma_t(x[row], part, dot);
                 }
             }
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
             __syncwarp();   // the next chunk overwrites the slice
         }
         if (has_row) {
-            y[row] = sum;
+            store_y(y, row, sum, ep.acc);
             if (ep.st) dot = fma_t(x[row], sum, dot);
         }
     }
@@ -659,7 +659,7 @@ template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
-    CooCarry* __restrict__ carry, const CgState* st) {
+    CooCarry* __restrict__ carry, const CgState* st, bool acc) {
     pdl_wait();
     pdl_trigger();
     if (st && st->done) return;
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     for (int i = threadIdx.x; i < nruns; i += kThreads) {
         const int32_t r = srow[rs[i]];
         const int32_t prev = (i > 0) ? srow[rs[i] - 1] : row_before;
-        for (int32_t z = prev + 1; z < r; ++z) y[z] = T(0);
+        for (int32_t z = prev + 1; z < r; ++z) zero_y(y, z, acc);
     }
     reduce_runs<VT>(a_s, x_s, rs, nruns, [&](int i, T sum) {
         const int32_t r = srow[rs[i]];
@@ -723,14 +723,14 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
         const bool to_tail = (i == nruns - 1) && cont_next;
         if (to_head) carry[w].head = to_f64_exact(sum);
         if (to_tail) carry[w].tail = to_f64_exact(sum);
-        if (!to_head && !to_tail) y[r] = sum;
+        if (!to_head && !to_tail) store_y(y, r, sum, acc);
     });
     if (threadIdx.x == 0) {
         carry[w].row_first = row_first;
         carry[w].row_last = row_last;
     }
     if (s + len == nnz)   // empty rows after the last entry
-        for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) y[z] = T(0);
+        for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) zero_y(y, z, acc);
 }
 
 // COO, run-vector kernel. Warp c takes the chunk of kCooVecChunk sorted entries
@@ -746,7 +746,7 @@ template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
-    int64_t nchunks, const CgState* st) {
+    int64_t nchunks, const CgState* st, bool acc) {
     pdl_wait();
     pdl_trigger();
     if (st && st->done) return;
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
             rs[pos] = k;
             rrow[pos] = r;
             if (r != prev)
-                for (int32_t z = prev + 1; z < r; ++z) y[z] = T(0);   // empty rows in between
+                for (int32_t z = prev + 1; z < r; ++z) zero_y(y, z, acc);   // empty rows in between
         }
         nr += __popc(ballot);
         carry_row = __shfl_sync(FULL, r, 31);
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
             const bool to_tail = (i == nr - 1) && cont_next;
             if (to_head) carry[c].head = to_f64_exact(sum);
             if (to_tail) carry[c].tail = to_f64_exact(sum);
-            if (!to_head && !to_tail) y[rrow[i]] = sum;
+            if (!to_head && !to_tail) store_y(y, rrow[i], sum, acc);
         }
     }
     if (lane == 0) {
@@ -818,14 +818,14 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
         carry[c].row_last = rrow[nr - 1];
     }
     if (c0 + len == nnz)   // empty rows after the last entry
-        for (int32_t z = rrow[nr - 1] + 1 + lane; z < nrows; z += 32) y[z] = T(0);
+        for (int32_t z = rrow[nr - 1] + 1 + lane; z < nrows; z += 32) zero_y(y, z, acc);
 }
 
 // Rows spanning windows: the window where such a row starts adds its tail, the heads of
 // the windows it covers entirely, and the head of the window where it ends, in order.
 template <typename T>
 __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_t nwin,
-                                      T* __restrict__ y, const CgState* st) {
+                                      T* __restrict__ y, const CgState* st, bool acc) {
     pdl_wait();
     pdl_trigger();
     if (st && st->done) return;
@@ -846,7 +846,7 @@ __global__ void spmv_coo_fixup_kernel(const CooCarry* __restrict__ carry, int64_
         if (d_single && d_next) ++v;
         else break;
     }
-    y[c.row_last] = (T)sum;
+    store_y(y, c.row_last, (T)sum, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -878,7 +878,7 @@ template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
-    int64_t nchunks, const CgState* st) {
+    int64_t nchunks, const CgState* st, bool acc) {
     pdl_wait();
     pdl_trigger();
     if (st && st->done) return;
@@ -937,9 +937,9 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
                     if (r != cur) {
                         if (h + k > 0) {   // close run `cur`
                             if (!closed) { head = sum; closed = true; }
-                            else y[cur] = sum;
+                            else store_y(y, cur, sum, acc);
                         }
-                        for (int32_t z = cur + 1; z < r; ++z) y[z] = T(0);   // empty rows
+                        for (int32_t z = cur + 1; z < r; ++z) zero_y(y, z, acc);   // empty rows
                         cur = r;
                         sum = T(0);
                     }
@@ -973,22 +973,22 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
         T tot = head;
         if (lane > 0 && first == prev_last) tot += prevS;
         if (first == chunk_first && cp) carry[c].head = to_f64_exact(tot);
-        else y[first] = tot;
+        else store_y(y, first, tot, acc);
     }
     if (lane < 31 && cnt > 0 && next_first != cur) {   // the last run ends at the lane's end
         if (cur == chunk_first && cp) carry[c].head = to_f64_exact(S);
-        else y[cur] = S;
+        else store_y(y, cur, S, acc);
     }
     if (lane == 31) {   // S is the chunk's last run
         const bool one_run = (chunk_first == chunk_last);
         if (cn) carry[c].tail = to_f64_exact(S);
         if (one_run && cp) carry[c].head = to_f64_exact(S);
-        if (!cn && !(one_run && cp)) y[chunk_last] = S;
+        if (!cn && !(one_run && cp)) store_y(y, chunk_last, S, acc);
         carry[c].row_first = chunk_first;
         carry[c].row_last = chunk_last;
     }
     if (c0 + len == nnz)   // empty rows after the last entry
-        for (int32_t z = chunk_last + 1 + lane; z < nrows; z += 32) y[z] = T(0);
+        for (int32_t z = chunk_last + 1 + lane; z < nrows; z += 32) zero_y(y, z, acc);
 }
 
 template <typename T>
@@ -1235,8 +1235,8 @@ static void launch_coo_windows(int32_t nrows, int64_t nnz, const int32_t* ai, co
                                const T* x, T* y, CooCarry* carry, int64_t nwin, cudaStream_t s, const CgState* st) {
     allow_smem<spmv_coo_stage_kernel<VT, T>>(coo_smem<T>());
     spmv_coo_stage_kernel<VT, T><<<(unsigned)nwin, kThreads, coo_smem<T>(), s>>>(nrows, nnz, ai, aj, av, x, y,
-                                                                                 carry, st);
-    if (nwin > 1) spmv_coo_fixup_kernel<T><<<blocks_for(nwin), kThreads, 0, s>>>(carry, nwin, y, st);
+                                                                                 carry, st, false);
+    if (nwin > 1) spmv_coo_fixup_kernel<T><<<blocks_for(nwin), kThreads, 0, s>>>(carry, nwin, y, st, false);
 }
 
 template <typename VT, typename T>
@@ -1246,16 +1246,16 @@ static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         nch = A->nchunks;
         launch_kernel(ep.pdl, spmv_coo_vec_kernel<VT, T>, (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)),
                       kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y,
-                      A->carry, nch, (const CgState*)ep.st);
+                      A->carry, nch, (const CgState*)ep.st, ep.acc);
     } else {
         nch = (A->nnz + kCooSegChunk - 1) / kCooSegChunk;
         launch_kernel(ep.pdl, spmv_coo_seg_kernel<VT, T>, (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)),
                       kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y,
-                      A->carry, nch, (const CgState*)ep.st);
+                      A->carry, nch, (const CgState*)ep.st, ep.acc);
     }
     if (nch > 1)
         launch_kernel(ep.pdl, spmv_coo_fixup_kernel<T>, blocks_for(nch), kThreads, 0, s, (const CooCarry*)A->carry,
-                      nch, y, (const CgState*)ep.st);
+                      nch, y, (const CgState*)ep.st, ep.acc);
     if (ep.st)
         launch_kernel(ep.pdl, dot_alpha_kernel<T>, (unsigned)vector_grid(A->nrows), kThreads, 0, s,
                       (int64_t)A->nrows, x, (const T*)y, ep);

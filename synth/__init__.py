@@ -125,6 +125,40 @@ def stencil27_torch(g: int, device, planes_per_chunk: int = 32):
     return rows, cols, vals
 
 
+def hpcg_rank_matrix(nx: int, ny: int, nz: int):
+    """The matrix one interior process holds in a distributed 27-point HPCG problem (the
+    paper's Sec. VI set-up): the process owns an nx x ny x nz block of a 3 x 3 x 3 block
+    decomposition (all 26 neighbours present). Rows are its cells, row i = ix + nx*iy +
+    nx*ny*iz; a neighbour inside the block is local column j < n = nx*ny*nz, a neighbour in
+    another block is a ghost column n + g, ghosts numbered in order of first appearance
+    scanning rows in order and, within a row, neighbours in ascending global index (the
+    external-column numbering of HPCG's halo set-up). Diagonal 26, off-diagonals -1; every row
+    has 27 entries. Returns (rows, cols, vals, n, n_ghost), triplets sorted by row."""
+    n = nx * ny * nz
+    r = np.arange(n, dtype=np.int64)
+    ix, iy, iz = r % nx, (r // nx) % ny, r // (nx * ny)
+    gx, gy = 3 * nx, 3 * ny
+    rows = np.repeat(r, 27)
+    cols = np.empty(27 * n, np.int64)
+    ghost_key = np.full(27 * n, -1, np.int64)
+    for k, (dz, dy, dx) in enumerate(_OFFSETS):   # ascending global index within a row
+        jx, jy, jz = ix + dx, iy + dy, iz + dz
+        inside = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+        cols[k::27] = np.where(inside, jx + nx * jy + nx * ny * jz, -1)
+        # global index of the neighbour in the 3nx x 3ny x 3nz grid (this block in the middle)
+        key = (jx + nx) + gx * (jy + ny) + gx * gy * (jz + nz)
+        ghost_key[k::27] = np.where(inside, -1, key)
+    is_ghost = ghost_key >= 0
+    keys = ghost_key[is_ghost]
+    uniq, first = np.unique(keys, return_index=True)
+    order = np.argsort(first, kind="stable")          # ghosts by first appearance
+    gid = np.empty(uniq.size, np.int64)
+    gid[order] = np.arange(uniq.size)
+    cols[is_ghost] = n + gid[np.searchsorted(uniq, keys)]
+    vals = np.where(cols == rows, 26.0, -1.0)
+    return rows.astype(np.int32), cols.astype(np.int32), vals, n, int(uniq.size)
+
+
 def stencil27_perturbed(g: int, seed: int = 1):
     return stencil27(g, perturb_seed=seed)
 

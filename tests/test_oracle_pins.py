@@ -359,3 +359,45 @@ def test_cg_ir_reaches_fp64_tolerance_with_bf16_values(orc):
     assert st == orc.OK and rel <= 1e-10 and outer >= 2
     true = np.linalg.norm(b - orc.spmv(C, x)) / np.linalg.norm(b)
     assert true <= 1e-10 and np.max(np.abs(x - 1)) < 1e-8
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 5), (6, 6, 6), (9, 5, 7)])
+def test_hpcg_rank_split_closed_forms(orc, dims):
+    """An interior process's matrix: 27 entries per row; the local part is the block's own
+    27-point stencil ((3nx-2)(3ny-2)(3nz-2) entries, bit-identical to the stencil generator for
+    cubes); ghosts are the (nx+2)(ny+2)(nz+2) - n cells around the block."""
+    nx, ny, nz = dims
+    r, c, v, n, ng = synth.hpcg_rank_matrix(nx, ny, nz)
+    assert ng == (nx + 2) * (ny + 2) * (nz + 2) - n
+    O = orc.canonicalize(n, n + ng, r, c, v)
+    assert O.nnz == 27 * n
+    loc, rem = orc.split_columns(O, n)
+    assert loc.nnz == (3 * nx - 2) * (3 * ny - 2) * (3 * nz - 2)
+    assert rem.nnz == 27 * n - loc.nnz and rem.ncols == ng
+    assert np.all(np.diff(loc.ai) >= 0) and np.all(np.diff(rem.ai) >= 0)
+    if nx == ny == nz:
+        sr, sc, sv = synth.stencil27(nx)
+        assert np.array_equal(loc.ai, sr) and np.array_equal(loc.aj, sc) and np.array_equal(loc.av, sv)
+    # b = A 1 is 26 - 26 = 0 on every row (all 27 neighbours exist)
+    assert np.all(orc.spmv(O, np.ones(n + ng)) == 0.0)
+    # every ghost column is used, and only by rows on the block's surface
+    assert np.array_equal(np.unique(rem.aj), np.arange(ng))
+    ix, iy, iz = rem.ai % nx, (rem.ai // nx) % ny, rem.ai // (nx * ny)
+    assert np.all((ix == 0) | (ix == nx - 1) | (iy == 0) | (iy == ny - 1) | (iz == 0) | (iz == nz - 1))
+
+
+def test_split_spmv_adds_up(orc):
+    """A x = local x[:c] + remote x[c:] exactly for integer data (every partial sum exact)."""
+    rng = np.random.default_rng(5)
+    nr, nc, c = 40, 70, 33
+    r = rng.integers(0, nr, 600)
+    col = rng.integers(0, nc, 600)
+    v = rng.integers(-4, 5, 600).astype(np.float64)
+    O = orc.canonicalize(nr, nc, r, col, v)
+    x = rng.integers(-3, 4, nc).astype(np.float64)
+    loc, rem = orc.split_columns(O, c)
+    assert loc.nnz + rem.nnz == O.nnz and loc.ncols == c and rem.ncols == nc - c
+    assert np.array_equal(orc.spmv(O, x), orc.spmv(loc, x[:c]) + orc.spmv(rem, x[c:]))
+    for cut in (0, nc):
+        a, b = orc.split_columns(O, cut)
+        assert (a.nnz, b.nnz) == ((0, O.nnz) if cut == 0 else (O.nnz, 0))
