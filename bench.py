@@ -609,6 +609,95 @@ def run_mixed(args, world, rank, local):
 
 
 # ---------------------------------------------------------------------------
+# local/remote split of one process's HPCG matrix
+# ---------------------------------------------------------------------------
+SPLIT_METRIC = "SpMV of one HPCG process's matrix: best single format vs local/remote split (ms)"
+
+
+def run_split(args, world, rank, local):
+    """One interior process of a 3 x 3 x 3 block decomposition of the 27-point problem (all 26
+    neighbours), as in the paper's distributed HPCG (Sec. VI): its matrix has a structured
+    local part and an unstructured ghost part. Times y = A x for the whole matrix in COO and
+    CSR (DIA cannot hold the ghost columns), and for every local format (COO, CSR, DIA) with
+    every remote format (COO, CSR): y = A_local x_local, then y += A_remote x_ghost. The
+    run-first tuner's choice for each part is reported beside the timings."""
+    import torch
+    import paper_2304_09511_gb300 as mspv
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    reps = max(args.steps, 10)
+
+    def time_ms(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            fn()
+        e0.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(s0.elapsed_time(e0) / reps, world)
+
+    out_sizes = []
+    for dims in ((48, 64, 64), (128, 128, 128)):
+        r, c, v, n, ng = synth.hpcg_rank_matrix(*dims)
+        A = mspv.Matrix.from_coo(n, n + ng, torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev),
+                                 torch.from_numpy(v).to(dev))
+        nnz = A.info["nnz"]
+        del r, c, v
+        x = torch.from_numpy(synth.uniform_x(n + ng, 0)).to(dev)
+        xl, xg = x[:n].contiguous(), x[n:].contiguous()
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        whole = {"coo": A, "csr": A.convert("csr")}
+        res = {"local_block": list(dims), "n": n, "ghosts": ng, "nnz": nnz}
+        res["whole_ms"] = {f: round(time_ms(lambda M=M: M.spmv(x, y)), 5) for f, M in whole.items()}
+        L0, R0 = A.split_columns(n)
+        res["local_nnz"], res["remote_nnz"] = L0.info["nnz"], R0.info["nnz"]
+        Ls = {"coo": L0, "csr": L0.convert("csr"), "dia": L0.convert("dia")}
+        Rs = {"coo": R0, "csr": R0.convert("csr")}
+        split = {}
+        for lf, L in Ls.items():
+            for rf, R in Rs.items():
+                def fn(L=L, R=R):
+                    L.spmv(xl, y)
+                    R.spmv_add(xg, y)
+                split[f"{lf}+{rf}"] = round(time_ms(fn), 5)
+        res["split_ms"] = split
+        lbest, lms = L0.tune_format(reps=20)
+        rbest, rms = R0.tune_format(reps=20)
+        res["tuner"] = {"local": lbest, "remote": rbest,
+                        "local_ms": {k: round(t, 5) for k, t in lms.items()},
+                        "remote_ms": {k: round(t, 5) for k, t in rms.items() if k != "dia"}}
+        best_whole = min(res["whole_ms"].items(), key=lambda kv: kv[1])
+        best_split = min(split.items(), key=lambda kv: kv[1])
+        res["best_whole"] = {"format": best_whole[0], "ms": best_whole[1]}
+        res["best_split"] = {"formats": best_split[0], "ms": best_split[1]}
+        res["tuned_split_ms"] = split[f"{lbest}+{rbest}"]
+        res["speedup_split_vs_whole"] = round(best_whole[1] / best_split[1], 3)
+        out_sizes.append(res)
+        for M in list(Ls.values()) + list(Rs.values()) + list(whole.values()):
+            M.close()
+    big = out_sizes[-1]
+    out = {"metric": SPLIT_METRIC, "value": big["tuned_split_ms"], "unit": "ms", "higher_is_better": False,
+           "n_gpus": world, "mode": "split", "scaling": "weak", "data": "synthetic", "dtype": "f64",
+           "config": {"workload": "one interior process (26 neighbours) of a 3x3x3 block decomposition of the "
+                                  "27-point problem, local blocks 48x64x64 and 128x128x128; value = tuned "
+                                  "local+remote SpMV on the 128^3 block", "reps": reps,
+                      "parallelism": f"replicas x{world}"},
+           "sizes": out_sizes}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 def oracle_workload(g):
@@ -691,10 +780,11 @@ def main():
     ap.add_argument("--ref-cg-iters", type=int, default=1,
                     help="CG iterations per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "selector", "mixed"], default="step",
+    ap.add_argument("--mode", choices=["step", "selector", "mixed", "split"], default="step",
                     help="step: the SpMV + CG step (default); selector: tuner labels, MLP "
                          "training and held-out regret, then the stencil end to end; mixed: FP64 "
-                         "CG vs FP32/BF16-value refinement on a large stencil")
+                         "CG vs FP32/BF16-value refinement on a large stencil; split: one HPCG "
+                         "process's matrix, whole vs local/remote formats")
     ap.add_argument("--mixed-grid", type=int, default=192, help="mixed mode: stencil grid")
     ap.add_argument("--matrices", type=int, default=2000, help="selector mode: synthetic matrices")
     ap.add_argument("--tune-reps", type=int, default=10, help="selector mode: timed SpMV per format")
@@ -712,6 +802,8 @@ def main():
         out = run_selector(args, world, rank, local)
     elif args.mode == "mixed":
         out = run_mixed(args, world, rank, local)
+    elif args.mode == "split":
+        out = run_split(args, world, rank, local)
     else:
         out = run_mspv(args, world, rank, local)
     if out is not None:
