@@ -1224,7 +1224,8 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     }
 #undef MSPV_CSR_CASE
     if (A->nlong > 0) {
-        const DotEpilogue lep{ep.st, ep.partials ? ep.partials + grid : nullptr, ep.pdl};
+        DotEpilogue lep = ep;   // same flags; its partials follow the V-lane kernel's
+        lep.partials = ep.partials ? ep.partials + grid : nullptr;
         launch_kernel(ep.pdl, spmv_csr_long_kernel<VT, T>, (unsigned)A->nlong, kThreads, 0, s, A->long_rows,
                       A->irp, A->aj, av, x, y, lep);
     }
