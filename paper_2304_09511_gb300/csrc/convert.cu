@@ -728,6 +728,8 @@ int32_t choose_coo_kernel(int32_t row_max) {
 mspv_status ensure_coo_carry(mspv_matrix* M) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
     M->coo_kernel = choose_coo_kernel(M->row_max);
+    const char* ch = std::getenv("MSPV_COO_CHUNK");
+    M->coo_chunk = (ch && std::atoi(ch) == 512) ? 512 : kCooVecChunk;
     M->nchunks = (M->nnz + kCooVecChunk - 1) / kCooVecChunk;
     MSPV_TRY(dev_alloc_n(&M->carry, M->nchunks > 0 ? M->nchunks : 1));
     M->bytes += (M->nchunks > 0 ? M->nchunks : 1) * (int64_t)sizeof(CooCarry);

@@ -733,16 +733,14 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
         for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) zero_y(y, z, acc);
 }
 
-// COO, run-vector kernel. Warp c takes the chunk of kCooVecChunk sorted entries
+// COO, run-vector kernel. Warp c takes the chunk of CHUNK (256 or 512) sorted entries
 // [c*C, (c+1)*C). Pass 1 (integer only): lanes read the row indices (coalesced), mark
 // where the row changes, and compact the run starts with ballots into the warp's slice
 // of shared memory, zeroing the rows skipped between runs. Pass 2: groups of 4 lanes
 // take one run each, lane-strided FMAs over its entries, then 2 shuffle-adds -- the CSR
 // V = 4 pattern, which on GB300 balances coalescing against FP64 issue slots. Runs cut
 // by a chunk edge leave partial sums in the carry record, added by the fix-up pass.
-constexpr int kCooVecPer = kCooVecChunk / 32;
-
-template <typename VT, typename T>
+template <typename VT, typename T, int CHUNK>
 __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, CooCarry* __restrict__ carry,
@@ -750,29 +748,29 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     pdl_wait();
     pdl_trigger();
     if (st && st->done) return;
-    __shared__ int32_t s_rs[kThreads / 32][kCooVecChunk + 1];
-    __shared__ int32_t s_row[kThreads / 32][kCooVecChunk];
+    __shared__ int32_t s_rs[kThreads / 32][CHUNK + 1];
+    __shared__ int32_t s_row[kThreads / 32][CHUNK];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * (kThreads / 32) + w;
     if (c >= nchunks) return;   // whole warp
-    const int64_t c0 = c * kCooVecChunk;
-    const int len = (int)((nnz - c0 < kCooVecChunk) ? nnz - c0 : kCooVecChunk);
+    const int64_t c0 = c * CHUNK;
+    const int len = (int)((nnz - c0 < CHUNK) ? nnz - c0 : CHUNK);
     const int32_t row_before = (c0 > 0) ? __ldg(ai + c0 - 1) : -1;
     const int32_t row_after = (c0 + len < nnz) ? __ldg(ai + c0 + len) : INT_MAX;
     int32_t* rs = s_rs[w];
     int32_t* rrow = s_row[w];
 
-    int32_t rv[kCooVecPer];
+    int32_t rv[(CHUNK / 32)];
 #pragma unroll
-    for (int q = 0; q < kCooVecPer; ++q) {
+    for (int q = 0; q < (CHUNK / 32); ++q) {
         const int k = q * 32 + lane;
         rv[q] = (k < len) ? __ldcs(ai + c0 + k) : INT_MAX;
     }
     int nr = 0;
     int32_t carry_row = row_before;
 #pragma unroll
-    for (int q = 0; q < kCooVecPer; ++q) {
+    for (int q = 0; q < (CHUNK / 32); ++q) {
         const int k = q * 32 + lane;
         const int32_t r = rv[q];
         int32_t prev = __shfl_up_sync(FULL, r, 1);
@@ -1244,10 +1242,16 @@ template <typename VT, typename T>
 static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
     int64_t nch;
     if (A->coo_kernel == 1) {
-        nch = A->nchunks;
-        launch_kernel(ep.pdl, spmv_coo_vec_kernel<VT, T>, (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)),
-                      kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj, static_cast<const VT*>(A->av), x, y,
-                      A->carry, nch, (const CgState*)ep.st, ep.acc);
+        const int chunk = A->coo_chunk == 512 ? 512 : kCooVecChunk;
+        nch = (A->nnz + chunk - 1) / chunk;   // <= A->nchunks, the carry records allocated
+        const unsigned g = (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32));
+        if (chunk == 512)
+            launch_kernel(ep.pdl, spmv_coo_vec_kernel<VT, T, 512>, g, kThreads, 0, s, A->nrows, A->nnz, A->ai,
+                          A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch, (const CgState*)ep.st, ep.acc);
+        else
+            launch_kernel(ep.pdl, spmv_coo_vec_kernel<VT, T, kCooVecChunk>, g, kThreads, 0, s, A->nrows, A->nnz,
+                          A->ai, A->aj, static_cast<const VT*>(A->av), x, y, A->carry, nch,
+                          (const CgState*)ep.st, ep.acc);
     } else {
         nch = (A->nnz + kCooSegChunk - 1) / kCooSegChunk;
         launch_kernel(ep.pdl, spmv_coo_seg_kernel<VT, T>, (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32)),
