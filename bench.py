@@ -585,7 +585,6 @@ def run_mixed(args, world, rank, local):
                 lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=1e-4, max_outer=30, maxit_inner=20000,
                                    inner_fp32=True))
             L.close()
-        M.close()
         if fmt == "dia":   # inner tolerance of the FP32-arithmetic solver (BF16 values)
             L = A.convert(fmt, "bf16")
             for itol in (1e-3, 1e-5, 1e-6):
@@ -593,6 +592,7 @@ def run_mixed(args, world, rank, local):
                     lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=itol, max_outer=40, maxit_inner=20000,
                                        inner_fp32=True))
             L.close()
+        M.close()
         results[fmt] = out
     clk = clocks.stop()
     best = min((v["ms"], f, k) for f, o in results.items() for k, v in o.items() if v["converged"])

@@ -153,7 +153,9 @@ __device__ __forceinline__ void finish_dot(T dot, DotEpilogue ep) {
 }
 
 // One thread per RPT consecutive rows, one CTA per strip of kThreads * RPT rows.
-template <typename VT, typename T>
+// ACC: y += A x (accumulating SpMV), a template argument so the y = A x path has no test
+// in its store.
+template <typename VT, typename T, bool ACC>
 __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
     const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, DotEpilogue ep) {
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             if (i0 + r < n) {
-                store_y(y, i0 + r, acc[r], ep.acc);
+                store_y(y, i0 + r, acc[r], ACC);
                 if (ep.st) d = fma_t(__ldg(x + i0 + r), acc[r], d);
             }
         }
@@ -1122,8 +1124,12 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         launch_kernel(ep.pdl, spmv_dia_f32_kernel<VT>, (unsigned)grid, kThreads, 0, s, A->nrows, A->ndiags,
                       A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
     } else {
-        launch_kernel(ep.pdl, spmv_dia_kernel<VT, T>, (unsigned)grid, kThreads, 0, s, A->nrows, A->ndiags,
-                      A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
+        if (ep.acc)
+            launch_kernel(ep.pdl, spmv_dia_kernel<VT, T, true>, (unsigned)grid, kThreads, 0, s, A->nrows,
+                          A->ndiags, A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
+        else
+            launch_kernel(ep.pdl, spmv_dia_kernel<VT, T, false>, (unsigned)grid, kThreads, 0, s, A->nrows,
+                          A->ndiags, A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
     }
 }
 
