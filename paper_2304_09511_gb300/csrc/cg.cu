@@ -190,8 +190,9 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(int64_t n, const doub
 }
 
 // x += alpha p; r -= alpha q; partial of r.r.
-__global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* __restrict__ x,
-                                                             double* __restrict__ r, const double* __restrict__ p,
+// r -= alpha q with the CTA partial of r.r. x is advanced by the p-update kernel, which reads
+// p anyway (x += alpha p there saves one pass over p per iteration).
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* __restrict__ r,
                                                              const double* __restrict__ q,
                                                              double* __restrict__ partials, const CgState* st) {
     pdl_wait();
@@ -200,7 +201,6 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
     const double alpha = st->alpha;
     double rr = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
         rr = fma(ri, ri, rr);
@@ -209,14 +209,23 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
 }
 
 // p = r + beta p
-__global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
-                                                              double* __restrict__ p, const CgState* st) {
+// Iteration `it`: x += alpha p, then p = r + beta p. Runs only when the iteration updated r
+// (its beta kernel counted it: st->iters == it); on the iteration that converged or reached
+// maxit only x is advanced.
+__global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, double* __restrict__ x,
+                                                              const double* __restrict__ r,
+                                                              double* __restrict__ p, const CgState* st,
+                                                              int32_t it) {
     pdl_wait();
     pdl_trigger();
-    if (st->done) return;
-    const double beta = st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
-        p[i] = fma(beta, p[i], r[i]);
+    if (st->iters != it) return;
+    const double alpha = st->alpha, beta = st->beta;
+    const bool more = !st->done;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double pi = p[i];
+        x[i] = fma(alpha, pi, x[i]);
+        if (more) p[i] = fma(beta, pi, r[i]);
+    }
 }
 
 // Iterative refinement: r = b - q; partials of r.r and b.b.
@@ -281,8 +290,7 @@ __global__ void __launch_bounds__(kThreads) cgf_init_kernel(int64_t n, const flo
     write_partial_f32(bb, pbb);
 }
 
-__global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* __restrict__ x,
-                                                              float* __restrict__ r, const float* __restrict__ p,
+__global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* __restrict__ r,
                                                               const float* __restrict__ q,
                                                               double* __restrict__ partials, const CgState* st) {
     pdl_wait();
@@ -297,21 +305,15 @@ __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* 
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     for (int64_t i = t0; i < n4; i += stride) {
-        float4 xv = reinterpret_cast<float4*>(x)[i];
         float4 rv = reinterpret_cast<float4*>(r)[i];
-        const float4 pv = reinterpret_cast<const float4*>(p)[i];
         const float4 qv = reinterpret_cast<const float4*>(q)[i];
-        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
         rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
         rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
-        reinterpret_cast<float4*>(x)[i] = xv;
         reinterpret_cast<float4*>(r)[i] = rv;
         rr = fmaf(rv.x, rv.x, rr); rr = fmaf(rv.y, rv.y, rr);
         rr = fmaf(rv.z, rv.z, rr); rr = fmaf(rv.w, rv.w, rr);
     }
     for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
-        x[i] = fmaf(alpha, p[i], x[i]);
         const float ri = fmaf(-alpha, q[i], r[i]);
         r[i] = ri;
         rr = fmaf(ri, ri, rr);
@@ -319,26 +321,43 @@ __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* 
     write_partial_f32(rr, partials);
 }
 
-__global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, const float* __restrict__ r,
-                                                               float* __restrict__ p, const CgState* st) {
+__global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, float* __restrict__ x,
+                                                               const float* __restrict__ r,
+                                                               float* __restrict__ p, const CgState* st,
+                                                               int32_t it) {
     pdl_wait();
     pdl_trigger();
-    if (st->done) return;
-    __shared__ float s_beta;
-    if (threadIdx.x == 0) s_beta = (float)st->beta;
+    if (st->iters != it) return;
+    __shared__ float s_ab[2];
+    if (threadIdx.x == 0) {
+        s_ab[0] = (float)st->alpha;
+        s_ab[1] = (float)st->beta;
+    }
     __syncthreads();
-    const float beta = s_beta;
+    const float alpha = s_ab[0], beta = s_ab[1];
+    const bool more = !st->done;
     const int64_t n4 = n / 4;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     for (int64_t i = t0; i < n4; i += stride) {
-        const float4 rv = reinterpret_cast<const float4*>(r)[i];
-        float4 pv = reinterpret_cast<float4*>(p)[i];
-        pv.x = fmaf(beta, pv.x, rv.x); pv.y = fmaf(beta, pv.y, rv.y);
-        pv.z = fmaf(beta, pv.z, rv.z); pv.w = fmaf(beta, pv.w, rv.w);
-        reinterpret_cast<float4*>(p)[i] = pv;
+        const float4 pv = reinterpret_cast<const float4*>(p)[i];
+        float4 xv = reinterpret_cast<float4*>(x)[i];
+        xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+        xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+        reinterpret_cast<float4*>(x)[i] = xv;
+        if (more) {
+            const float4 rv = reinterpret_cast<const float4*>(r)[i];
+            float4 np;
+            np.x = fmaf(beta, pv.x, rv.x); np.y = fmaf(beta, pv.y, rv.y);
+            np.z = fmaf(beta, pv.z, rv.z); np.w = fmaf(beta, pv.w, rv.w);
+            reinterpret_cast<float4*>(p)[i] = np;
+        }
     }
-    for (int64_t i = 4 * n4 + t0; i < n; i += stride) p[i] = fmaf(beta, p[i], r[i]);
+    for (int64_t i = 4 * n4 + t0; i < n; i += stride) {
+        const float pi = p[i];
+        x[i] = fmaf(alpha, pi, x[i]);
+        if (more) p[i] = fmaf(beta, pi, r[i]);
+    }
 }
 
 // Refinement glue: r32 = (float)(r * scale); x += scale * (double)d32.
@@ -436,10 +455,10 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
             MSPV_SCALAR_LAUNCH(pdl, cg_alpha_kernel, P, s, (const double*)w.partials, P, w.st);
-            launch_kernel(pdl, update, Gu, kThreads, 0, s, n, x, r, (const V*)p, (const V*)q, w.partials,
-                          (const CgState*)w.st);
+            launch_kernel(pdl, update, Gu, kThreads, 0, s, n, r, (const V*)q, w.partials, (const CgState*)w.st);
             MSPV_SCALAR_LAUNCH(pdl, cg_beta_kernel, (int64_t)Gu, s, (const double*)w.partials, (int64_t)Gu, w.st);
-            launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, (const V*)r, p, (const CgState*)w.st);
+            launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, x, (const V*)r, p, (const CgState*)w.st,
+                          (int32_t)(launched + k + 1));
         }
         MSPV_CUDA_TRY(cudaGetLastError());
         launched += batch;
