@@ -272,34 +272,73 @@ def run_mspv(args, world, rank, local):
     # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update
     launches_per_step = coo_launches + 1 + 1 + (3 + 5 * args.cg_iters)
 
-    # end to end through the public API with host buffers: H2D of x and b, D2H of the
-    # three SpMV results and the CG solution, inside the timed region
+    # end to end through the public API with host buffers: every step copies its x and b from
+    # pinned host memory and reads the three SpMV results and the CG solution back, all inside
+    # the timed region. The copies run on a second stream: step k+1's inputs are fetched into
+    # the other half of a double buffer while step k computes, and each result is read back as
+    # soon as it is ready; events order every copy against the kernels that use its buffer.
     x_h = torch.from_numpy(synth.uniform_x(n, 0)).pin_memory()
     b_h = b.cpu().pin_memory()
     outs_h = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
-    x_d = torch.empty_like(x)
-    b_d = torch.empty_like(b)
+    x_d = [torch.empty_like(x) for _ in range(2)]
+    b_d = [torch.empty_like(b) for _ in range(2)]
+    xcg_d = [torch.empty_like(xcg) for _ in range(2)]
+    copy = torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]    # main stream finished with input buffer
+    ev_y = {f: torch.cuda.Event() for f in ("coo", "csr", "dia")}
+    ev_y_read = {f: torch.cuda.Event() for f in ("coo", "csr", "dia")}
+    ev_x = [torch.cuda.Event() for _ in range(2)]
+    ev_x_read = [torch.cuda.Event() for _ in range(2)]
+    for e in list(ev_used) + list(ev_y_read.values()) + list(ev_x_read):
+        e.record(stream)
 
-    def e2e_step():
-        x_d.copy_(x_h, non_blocking=True)
-        b_d.copy_(b_h, non_blocking=True)
+    def fetch(k):
+        j = k % 2
+        copy.wait_event(ev_used[j])
+        with torch.cuda.stream(copy):
+            x_d[j].copy_(x_h, non_blocking=True)
+            b_d[j].copy_(b_h, non_blocking=True)
+        ev_in[j].record(copy)
+
+    def e2e_step(k, last):
+        j = k % 2
+        if not last:
+            fetch(k + 1)
+        stream.wait_event(ev_in[j])
         for i, f in enumerate(("coo", "csr", "dia")):
-            mats[f].spmv(x_d, y[f])
-            outs_h[i].copy_(y[f], non_blocking=True)
-        xcg.zero_()
-        D.cg(b_d, x=xcg, tol=0.0, maxit=args.cg_iters)
-        outs_h[3].copy_(xcg, non_blocking=True)
+            stream.wait_event(ev_y_read[f])
+            mats[f].spmv(x_d[j], y[f])
+            ev_y[f].record(stream)
+            copy.wait_event(ev_y[f])
+            with torch.cuda.stream(copy):
+                outs_h[i].copy_(y[f], non_blocking=True)
+            ev_y_read[f].record(copy)
+        stream.wait_event(ev_x_read[j])
+        xcg_d[j].zero_()
+        D.cg(b_d[j], x=xcg_d[j], tol=0.0, maxit=args.cg_iters)
+        ev_used[j].record(stream)
+        ev_x[j].record(stream)
+        copy.wait_event(ev_x[j])
+        with torch.cuda.stream(copy):
+            outs_h[3].copy_(xcg_d[j], non_blocking=True)
+        ev_x_read[j].record(copy)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+    def e2e_run(steps):
+        fetch(0)
+        for k in range(steps):
+            e2e_step(k, k == steps - 1)
+        stream.wait_stream(copy)
+
+    e2e_run(max(1, args.warmup))
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     s2 = torch.cuda.Event(enable_timing=True)
     e2 = torch.cuda.Event(enable_timing=True)
     s2.record(stream)
-    for _ in range(K):
-        e2e_step()
+    copy.wait_event(s2)
+    e2e_run(K)
     e2.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(s2.elapsed_time(e2), world) / K
