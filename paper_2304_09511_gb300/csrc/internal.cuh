@@ -121,8 +121,8 @@ struct CgState {
     int32_t maxit;
     int32_t done;    // nonzero once converged, at maxit, or broken down
     int32_t phase;   // CgPhase
-    uint32_t ticket; // last-block counter of the fused reductions (reset by the last block)
-    uint32_t pad;
+    uint32_t pad0;
+    uint32_t pad1;
 };
 
 // An SpMV kernel's optional epilogue for CG: each CTA writes its partial of the dot x.y
@@ -334,31 +334,5 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
     return t;
 }
 
-// Fused cross-CTA reduction: every CTA posts its partial; the last CTA to arrive
-// (atomic ticket, no waiting) sums all partials in index order, so the result is
-// deterministic. Returns true in exactly one CTA, where thread 0 holds *total.
-__device__ __forceinline__ bool last_block_total(double partial, double* partials,
-                                                 uint32_t* ticket, double* total) {
-    __shared__ double s_red[kThreads];
-    __shared__ bool s_last;
-    double bsum = block_sum(partial, s_red);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = bsum;
-        __threadfence();
-        uint32_t t = atomicAdd(ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    double acc = 0.0;
-    for (uint32_t b = threadIdx.x; b < gridDim.x; b += kThreads) acc += __ldcg(partials + b);
-    double tot = block_sum(acc, s_red);
-    if (threadIdx.x == 0) {
-        *total = tot;
-        *ticket = 0u;
-    }
-    return true;
-}
 
 }  // namespace mspv
