@@ -30,8 +30,6 @@
 #include <cstdlib>
 #include <string>
 
-#include <type_traits>
-
 #include "internal.cuh"
 
 namespace mspv {
@@ -796,36 +794,25 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
 
     const bool cont_prev = (row_before == rrow[0]);
     const bool cont_next = (row_after == rrow[nr - 1]);
-    // One pass: groups of V lanes take runs i0, i0 + 1, ... (at most 32 / V of them).
-    auto pass = [&](auto vc, int i0, int count) {
-        constexpr int V = decltype(vc)::value;
-        const int grp = lane / V, sub = lane % V;
+    const int grp = lane >> 2, sub = lane & 3;
+    for (int i0 = 0; i0 < nr; i0 += 8) {
         const int i = i0 + grp;
         T sum = T(0);
-        if (grp < count) {
+        if (i < nr) {
             const int b = rs[i], e = rs[i + 1];
-            for (int j = b + sub; j < e; j += V)
+            for (int j = b + sub; j < e; j += 4)
                 sum = fma_t(convert_value<T>(__ldcs(av + c0 + j)), __ldg(x + __ldcs(aj + c0 + j)), sum);
         }
-#pragma unroll
-        for (int o = V / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-        if (sub == 0 && grp < count) {
+        sum += __shfl_xor_sync(FULL, sum, 1);
+        sum += __shfl_xor_sync(FULL, sum, 2);
+        if (sub == 0 && i < nr) {
             const bool to_head = (i == 0) && cont_prev;
             const bool to_tail = (i == nr - 1) && cont_next;
             if (to_head) carry[c].head = to_f64_exact(sum);
             if (to_tail) carry[c].tail = to_f64_exact(sum);
             if (!to_head && !to_tail) store_y(y, rrow[i], sum, acc);
         }
-    };
-    // Full passes of 8 runs x 4 lanes; the last runs (fewer than 8) get more lanes each, so a
-    // nearly empty pass does not cost a full pass of FP64 issue slots.
-    int i0 = 0;
-    for (; i0 + 8 <= nr; i0 += 8) pass(std::integral_constant<int, 4>{}, i0, 8);
-    const int rest = nr - i0;   // warp-uniform
-    if (rest == 1) pass(std::integral_constant<int, 32>{}, i0, 1);
-    else if (rest == 2) pass(std::integral_constant<int, 16>{}, i0, 2);
-    else if (rest > 2 && rest <= 4) pass(std::integral_constant<int, 8>{}, i0, rest);
-    else if (rest > 4) pass(std::integral_constant<int, 4>{}, i0, rest);
+    }
     if (lane == 0) {
         carry[c].row_first = rrow[0];
         carry[c].row_last = rrow[nr - 1];
