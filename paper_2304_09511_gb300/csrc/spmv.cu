@@ -45,11 +45,10 @@ static_assert(kCooWindow <= kStageCap, "COO window must fit the staging buffers"
 // ---------------------------------------------------------------------------
 template <typename VT, typename T> struct DiaVec;
 template <> struct DiaVec<double, double> {
-    static constexpr int RPT = 4;   // 4 rows per thread: two 128-bit loads per diagonal
+    static constexpr int RPT = 2;
     __device__ __forceinline__ static void load(const double* p, double (&v)[RPT]) {
-        const double2 t0 = __ldcs(reinterpret_cast<const double2*>(p));
-        const double2 t1 = __ldcs(reinterpret_cast<const double2*>(p) + 1);
-        v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+        const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+        v[0] = t.x; v[1] = t.y;
     }
 };
 template <> struct DiaVec<float, double> {
@@ -1097,7 +1096,7 @@ static void allow_smem(size_t bytes) {
 // CTAs run on consecutive strips, so the CTAs in flight read one contiguous stretch of
 // each diagonal and of x (DRAM and L2 friendly). Spreading one wave of CTAs over distant
 // equal row ranges instead balances the tail but measured ~10% slower on GB300.
-static int64_t dia_rpt(int vt) { return vt == MSPV_F64 ? 4 : (vt == MSPV_F32 ? 4 : 8); }
+static int64_t dia_rpt(int vt) { return vt == MSPV_F64 ? 2 : (vt == MSPV_F32 ? 4 : 8); }
 
 static int64_t csr_grid_for(const mspv_matrix* A);
 
