@@ -178,3 +178,18 @@ def test_fp32_inner_needs_low_precision_values(mspv, stencil16):
     D = A.convert("dia")
     with pytest.raises(mspv.MspvError, match="EFORMAT"):
         D.cg_ir(D, dev(np.ones(n)), inner_fp32=True)
+
+
+def test_cg_with_an_unaligned_solution_vector(mspv, stencil16):
+    """x may be any 8-byte-aligned view (here offset by one element); the iterate is the
+    same as with an aligned x."""
+    g, n, A, O = stencil16
+    D = A.convert("dia")
+    b = dev(synth.uniform_x(n, 4))
+    buf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    xu = buf[1:]
+    assert xu.data_ptr() % 16 == 8
+    r1 = D.cg(b, x=xu, tol=0.0, maxit=15)
+    r2 = D.cg(b, tol=0.0, maxit=15)
+    assert r1.iters == r2.iters == 15
+    assert torch.equal(r1.x, r2.x)
