@@ -200,26 +200,9 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
     if (st->done) return;
     const double alpha = st->alpha;
     double rr = 0.0;
-    // r and q are the handle's own (256-byte aligned) vectors: 128-bit accesses, two pairs
-    // in flight per thread
-    const int64_t n2 = n / 2;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    const int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    double2* r2 = reinterpret_cast<double2*>(r);
-    const double2* q2 = reinterpret_cast<const double2*>(q);
-#pragma unroll 2
-    for (int64_t i = t0; i < n2; i += stride) {
-        double2 rv = r2[i];
-        const double2 qv = q2[i];
-        rv.x = fma(-alpha, qv.x, rv.x);
-        rv.y = fma(-alpha, qv.y, rv.y);
-        r2[i] = rv;
-        rr = fma(rv.x, rv.x, rr);
-        rr = fma(rv.y, rv.y, rr);
-    }
-    if ((n & 1) && t0 == 0) {
-        const double ri = fma(-alpha, q[n - 1], r[n - 1]);
-        r[n - 1] = ri;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
         rr = fma(ri, ri, rr);
     }
     write_partial(rr, partials);
@@ -229,10 +212,6 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
 // Iteration `it`: x += alpha p, then p = r + beta p. Runs only when the iteration updated r
 // (its beta kernel counted it: st->iters == it); on the iteration that converged or reached
 // maxit only x is advanced.
-// Iteration `it`: x += alpha p, then p = r + beta p. Runs only when the iteration updated r
-// (its beta kernel counted it: st->iters == it); on the iteration that converged or reached
-// maxit only x is advanced. x is the caller's vector: 128-bit accesses when it is 16-byte
-// aligned, scalar otherwise (a warp-uniform choice).
 __global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, double* __restrict__ x,
                                                               const double* __restrict__ r,
                                                               double* __restrict__ p, const CgState* st,
@@ -242,29 +221,7 @@ __global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, double*
     if (st->iters != it) return;
     const double alpha = st->alpha, beta = st->beta;
     const bool more = !st->done;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    const int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    int64_t tail = 0;   // first element left to the scalar loop
-    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-        const int64_t n2 = n / 2;
-        double2* x2 = reinterpret_cast<double2*>(x);
-        double2* p2 = reinterpret_cast<double2*>(p);
-        const double2* r2 = reinterpret_cast<const double2*>(r);
-#pragma unroll 2
-        for (int64_t i = t0; i < n2; i += stride) {
-            const double2 pv = p2[i];
-            double2 xv = x2[i];
-            xv.x = fma(alpha, pv.x, xv.x);
-            xv.y = fma(alpha, pv.y, xv.y);
-            x2[i] = xv;
-            if (more) {
-                const double2 rv = r2[i];
-                p2[i] = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
-            }
-        }
-        tail = 2 * n2;
-    }
-    for (int64_t i = tail + t0; i < n; i += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const double pi = p[i];
         x[i] = fma(alpha, pi, x[i]);
         if (more) p[i] = fma(beta, pi, r[i]);
