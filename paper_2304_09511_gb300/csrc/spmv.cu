@@ -26,7 +26,6 @@
 // No floating-point atomics anywhere: y is bit-identical run to run. Each kernel can
 // fuse CG's p.q into its epilogue (DotEpilogue); the last CTA reduces the per-CTA
 // partials in index order and forms alpha.
-#include <algorithm>
 #include <climits>
 #include <cstdlib>
 #include <string>
@@ -80,15 +79,15 @@ template <> struct DiaVec<float, float> {
     }
 };
 template <> struct DiaVec<__nv_bfloat16, float> {
-    // 4 rows per thread (an 8-byte value load per diagonal): with 8 rows the kernel needs
-    // 48 registers and the grid fills only 1.35 waves at 128^3, half a wave idle
-    static constexpr int RPT = 4;
+    static constexpr int RPT = 8;
     __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[RPT]) {
-        const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
-        v[0] = __uint_as_float(t.x << 16);
-        v[1] = __uint_as_float(t.x & 0xffff0000u);
-        v[2] = __uint_as_float(t.y << 16);
-        v[3] = __uint_as_float(t.y & 0xffff0000u);
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
     }
 };
 
@@ -214,7 +213,7 @@ template <typename VT>
 __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
     const VT* __restrict__ av, const float* __restrict__ x, float* __restrict__ y, DotEpilogue ep) {
-    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 or BF16 values)
+    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 values) or 8 (BF16 values)
     constexpr int NW = RPT / 4 + 1;               // windows covering RPT values at any shift
     pdl_wait();
     pdl_trigger();
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
         }
     }
     float d = 0.0f;
-    if (!ep.acc && i0 + RPT <= n) {
+    if (i0 + RPT <= n) {
 #pragma unroll
         for (int q = 0; q < RPT / 4; ++q) {
             reinterpret_cast<float4*>(y + i0)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
@@ -1097,15 +1096,7 @@ static void allow_smem(size_t bytes) {
 // CTAs run on consecutive strips, so the CTAs in flight read one contiguous stretch of
 // each diagonal and of x (DRAM and L2 friendly). Spreading one wave of CTAs over distant
 // equal row ranges instead balances the tail but measured ~10% slower on GB300.
-// Rows per thread of the DIA kernels for a value type, the smaller of the FP64-arithmetic
-// and FP32-arithmetic instantiations (the larger grid bounds the CG partial sums).
-static int64_t dia_rpt(int vt) {
-    switch (vt) {
-        case MSPV_F64: return DiaVec<double, double>::RPT;
-        case MSPV_F32: return std::min(DiaVec<float, double>::RPT, DiaVec<float, float>::RPT);
-        default: return std::min(DiaVec<__nv_bfloat16, double>::RPT, DiaVec<__nv_bfloat16, float>::RPT);
-    }
-}
+static int64_t dia_rpt(int vt) { return vt == MSPV_F64 ? 2 : (vt == MSPV_F32 ? 4 : 8); }
 
 static int64_t csr_grid_for(const mspv_matrix* A);
 
