@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
         }
     }
     float d = 0.0f;
-    if (i0 + RPT <= n) {
+    if (!ep.acc && i0 + RPT <= n) {   // the vector store overwrites; accumulation goes below
 #pragma unroll
         for (int q = 0; q < RPT / 4; ++q) {
             reinterpret_cast<float4*>(y + i0)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
