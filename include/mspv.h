@@ -187,6 +187,14 @@ MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t ncols, int64_t
                                            void* stream);
 
 /*
+ * y = A x in FP32 arithmetic (the inner SpMV of mspv_cg_solve_ir with inner_fp32 = 1): A stores
+ * FP32 or BF16 values (EFORMAT for FP64 values), x (ncols) and y (nrows) are DEVICE FP32 arrays,
+ * both 16-byte aligned (EINVAL otherwise), x and y must not overlap. Products and sums in FP32
+ * (BF16 values widened exactly). Asynchronous on `stream`.
+ */
+MSPV_API mspv_status mspv_spmv_f32(mspv_matrix_t A, const float* x, float* y, void* stream);
+
+/*
  * y += A x: the accumulating form of mspv_spmv (same arguments, layouts and errors). Rows of A
  * without entries leave y unchanged. With mspv_split_columns it forms y = A_local x_local +
  * A_remote x_remote, one call per part.

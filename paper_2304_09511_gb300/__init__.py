@@ -184,6 +184,18 @@ class Matrix:
         _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
         return CgResult(x, st, it.value, rr.value)
 
+    def spmv_f32(self, x, y=None, stream=None):
+        """y = A x in FP32 arithmetic for FP32/BF16-valued handles (float32 CUDA tensors,
+        16-byte aligned)."""
+        import torch
+        nr, nc = self.shape
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.numel() == nc):
+            raise TypeError("x must be a CUDA float32 tensor with ncols entries")
+        if y is None:
+            y = torch.empty(nr, dtype=torch.float32, device=x.device)
+        _lib.check(load().mspv_spmv_f32(self._h, x.data_ptr(), y.data_ptr(), stream_handle(stream)))
+        return y
+
     def spmv_add(self, x, y, stream=None):
         """y += A x (device float64 tensors); returns y."""
         _check_vec(x, self.shape[1])

@@ -54,6 +54,7 @@ SIGNATURES = {
     "mspv_csr_vector_width": (i32, [dbl, dbl, i32]),
     "mspv_version": (i32, []),
     "mspv_spmv_add": (i32, [vp, vp, vp, vp]),
+    "mspv_spmv_f32": (i32, [vp, vp, vp, vp]),
     "mspv_split_columns": (i32, [vp, i32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
     "mspv_features": (i32, [vp, vp, vp]),
     "mspv_tune_format": (i32, [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_int)]),

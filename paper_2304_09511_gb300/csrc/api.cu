@@ -262,6 +262,17 @@ MSPV_API mspv_status mspv_export(mspv_matrix_t A, int32_t* idx0, int32_t* idx1, 
     MSPV_GUARD_END
 }
 
+MSPV_API mspv_status mspv_spmv_f32(mspv_matrix_t A, const float* x, float* y, void* stream) {
+    MSPV_GUARD_BEGIN
+    if (!A) return set_error(MSPV_EINVAL, "spmv_f32: A is NULL");
+    if ((!x && A->ncols > 0) || (!y && A->nrows > 0)) return set_error(MSPV_EINVAL, "spmv_f32: NULL vector");
+    if (x == y && A->nrows > 0) return set_error(MSPV_EINVAL, "spmv_f32: x and y must not overlap");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+        return set_error(MSPV_EINVAL, "spmv_f32: x and y must be 16-byte aligned");
+    return launch_spmv_f32(A, x, y, as_stream(stream), DotEpilogue{nullptr, nullptr});
+    MSPV_GUARD_END
+}
+
 MSPV_API mspv_status mspv_spmv_add(mspv_matrix_t A, const double* x, double* y, void* stream) {
     MSPV_GUARD_BEGIN
     if (!A) return set_error(MSPV_EINVAL, "spmv_add: A is NULL");

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -603,6 +604,24 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
         dia_offsets_kernel<<<grid_for(span), kThreads, 0, s>>>(flags.as<int32_t>(), map.as<int32_t>(), span, n, M->doff);
         MSPV_CUDA_TRY(cudaGetLastError());
     }
+    // runs of consecutive offsets (at most 3 long): the FP32-arithmetic kernel reads one x
+    // window per run instead of one per diagonal
+    if (nd > 0) {
+        std::vector<int32_t> off(nd);
+        MSPV_CUDA_TRY(cudaMemcpyAsync(off.data(), M->doff, sizeof(int32_t) * nd, cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int2> runs;
+        for (int32_t j = 0; j < nd;) {
+            int32_t len = 1;
+            while (j + len < nd && len < 3 && off[j + len] == off[j] + len) ++len;
+            runs.push_back(make_int2(j, len));
+            j += len;
+        }
+        M->ndruns = (int32_t)runs.size();
+        MSPV_TRY(dev_alloc(reinterpret_cast<void**>(&M->druns), sizeof(int2) * runs.size()));
+        M->bytes += (int64_t)(sizeof(int2) * runs.size());
+        MSPV_CUDA_TRY(cudaMemcpyAsync(M->druns, runs.data(), sizeof(int2) * runs.size(), cudaMemcpyHostToDevice, s));
+    }
     zero_bytes_kernel<<<grid_for((int64_t)(avbytes / 16)), kThreads, 0, s>>>((uint4*)M->av, (int64_t)(avbytes / 16));
     MSPV_CUDA_TRY(cudaGetLastError());
     if (nnz > 0) {
@@ -767,11 +786,13 @@ mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, do
 
 void free_matrix(mspv_matrix* M) {
     auto f = [](void* p) { if (p) dev_free(p, 0); };
-    f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->av); f(M->carry); f(M->row_block); f(M->long_rows);
+    f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->druns); f(M->av); f(M->carry); f(M->row_block); f(M->long_rows);
     f(M->cg.r); f(M->cg.p); f(M->cg.q); f(M->cg.partials); f(M->cg.st);
     f(M->cg.rf); f(M->cg.pf); f(M->cg.qf);
     if (M->cg.host_st) cudaFreeHost(M->cg.host_st);
     M->ai = M->aj = M->irp = M->doff = nullptr;
+    M->druns = nullptr;
+    M->ndruns = 0;
     M->av = nullptr;
     M->carry = nullptr;
     M->row_block = nullptr;

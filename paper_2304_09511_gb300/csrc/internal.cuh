@@ -235,6 +235,8 @@ struct mspv_matrix {
     int32_t* aj = nullptr;    // COO / CSR columns
     int32_t* irp = nullptr;   // CSR row pointers
     int32_t* doff = nullptr;  // DIA offsets
+    int2* druns = nullptr;    // DIA: runs of consecutive offsets (first diagonal, length <= 3)
+    int32_t ndruns = 0;
     void* av = nullptr;       // values (value_type)
     int64_t av_count = 0;
 

@@ -26,6 +26,7 @@
 // No floating-point atomics anywhere: y is bit-identical run to run. Each kernel can
 // fuse CG's p.q into its epilogue (DotEpilogue); the last CTA reduces the per-CTA
 // partials in index order and forms alpha.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 #include <string>
@@ -79,15 +80,13 @@ template <> struct DiaVec<float, float> {
     }
 };
 template <> struct DiaVec<__nv_bfloat16, float> {
-    static constexpr int RPT = 8;
+    static constexpr int RPT = 4;   // an 8-byte value load per diagonal, as many rows as FP32
     __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[RPT]) {
-        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[2 * k] = __uint_as_float(w[k] << 16);
-            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-        }
+        const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xffff0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xffff0000u);
     }
 };
 
@@ -198,10 +197,11 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_kernel(
 }
 
 // FP32-arithmetic DIA (inner solver of mixed-precision refinement; x and y are the
-// library's own 16-byte-aligned FP32 vectors). Memory-bound rather than FP64-bound, so
-// load instructions matter: for each diagonal the RPT values x[i0+off .. i0+off+RPT) are
-// read as NW aligned 128-bit windows starting at i0+off rounded down to a multiple of
-// 4, and picked out by the shift m = off & 3, which is the same for the whole warp.
+// library's own 16-byte-aligned FP32 vectors). Bound by loads, not arithmetic: the diagonals
+// go in runs of consecutive offsets (at most 3, found at conversion; the 27-point stencil has
+// 9 runs of 3), and one 12-float x window serves a whole run: the window starts at the first
+// offset's index rounded down to a multiple of 4 and each diagonal t of the run picks its
+// values at the shift m + t (m = that offset's index & 3, the same for the whole warp).
 template <int M, int RPT, int W>
 __device__ __forceinline__ void dia_f32_fma(const float (&a)[RPT], const float (&w)[W], float (&acc)[RPT]) {
     static_assert(M + RPT <= W, "window too short for the shift");
@@ -211,10 +211,11 @@ __device__ __forceinline__ void dia_f32_fma(const float (&a)[RPT], const float (
 
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
-    int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff,
-    const VT* __restrict__ av, const float* __restrict__ x, float* __restrict__ y, DotEpilogue ep) {
-    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 values) or 8 (BF16 values)
-    constexpr int NW = RPT / 4 + 1;               // windows covering RPT values at any shift
+    int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff, const int2* __restrict__ runs,
+    int32_t nruns, const VT* __restrict__ av, const float* __restrict__ x, float* __restrict__ y, DotEpilogue ep) {
+    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 or BF16 values)
+    static_assert(RPT == 4, "the run window is sized for 4 rows per thread");
+    constexpr int W = 12;                          // shift m + t <= 5, plus 4 rows, in 3 float4
     pdl_wait();
     pdl_trigger();
     if (ep.st && ep.st->done) return;
@@ -227,48 +228,66 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
     for (int r = 0; r < RPT; ++r) acc[r] = 0.0f;
     if (i0 < n) {
         const VT* col = av + i0;
-#pragma unroll 2
-        for (int j = 0; j < ndiags; ++j) {
-            const int32_t off = (j < kDiaSmemDiags) ? s_off[j] : __ldg(doff + j);
-            float a[RPT];
-            DiaVec<VT, float>::load(col + (int64_t)j * npad, a);
+        for (int q = 0; q < nruns; ++q) {
+            const int2 run = __ldg(runs + q);
+            const int j0 = run.x, len = run.y;
+            float a[3][RPT];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                if (t < len) {
+                    DiaVec<VT, float>::load(col + (int64_t)(j0 + t) * npad, a[t]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) a[t][r] = 0.0f;
+                }
+            }
+            const int32_t off = (j0 < kDiaSmemDiags) ? s_off[j0] : __ldg(doff + j0);
             const int64_t k0 = i0 + off;
             const int m = (int)(k0 & 3);
             const int64_t base = k0 - m;
-            if (base >= 0 && base + 4 * NW <= n) {
-                float w[4 * NW];
+            if (base >= 0 && base + W <= n) {
+                float w[W];
 #pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    const float4 t = __ldg(reinterpret_cast<const float4*>(x + base) + q);
-                    w[4 * q] = t.x; w[4 * q + 1] = t.y; w[4 * q + 2] = t.z; w[4 * q + 3] = t.w;
+                for (int u = 0; u < W / 4; ++u) {
+                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(x + base) + u);
+                    w[4 * u] = t4.x; w[4 * u + 1] = t4.y; w[4 * u + 2] = t4.z; w[4 * u + 3] = t4.w;
                 }
-                switch (m) {   // uniform across the warp
-                    case 0: dia_f32_fma<0>(a, w, acc); break;
-                    case 1: dia_f32_fma<1>(a, w, acc); break;
-                    case 2: dia_f32_fma<2>(a, w, acc); break;
-                    default: dia_f32_fma<3>(a, w, acc); break;
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (t < len) {
+                        switch (m + t) {   // uniform across the warp
+                            case 0: dia_f32_fma<0>(a[t], w, acc); break;
+                            case 1: dia_f32_fma<1>(a[t], w, acc); break;
+                            case 2: dia_f32_fma<2>(a[t], w, acc); break;
+                            case 3: dia_f32_fma<3>(a[t], w, acc); break;
+                            case 4: dia_f32_fma<4>(a[t], w, acc); break;
+                            default: dia_f32_fma<5>(a[t], w, acc); break;
+                        }
+                    }
                 }
             } else {   // a strip touching either end of x
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    const int64_t k = k0 + r;
-                    if (k >= 0 && k < n) acc[r] = fmaf(a[r], __ldg(x + k), acc[r]);
+                for (int t = 0; t < 3; ++t) {
+                    if (t < len) {
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            const int64_t k = k0 + t + r;
+                            if (k >= 0 && k < n) acc[r] = fmaf(a[t][r], __ldg(x + k), acc[r]);
+                        }
+                    }
                 }
             }
         }
     }
     float d = 0.0f;
     if (!ep.acc && i0 + RPT <= n) {   // the vector store overwrites; accumulation goes below
-#pragma unroll
-        for (int q = 0; q < RPT / 4; ++q) {
-            reinterpret_cast<float4*>(y + i0)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-            if (ep.st) {
-                const float4 xv = __ldg(reinterpret_cast<const float4*>(x + i0) + q);
-                d = fmaf(xv.x, acc[4 * q], d);
-                d = fmaf(xv.y, acc[4 * q + 1], d);
-                d = fmaf(xv.z, acc[4 * q + 2], d);
-                d = fmaf(xv.w, acc[4 * q + 3], d);
-            }
+        reinterpret_cast<float4*>(y + i0)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        if (ep.st) {
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(x + i0));
+            d = fmaf(xv.x, acc[0], d);
+            d = fmaf(xv.y, acc[1], d);
+            d = fmaf(xv.z, acc[2], d);
+            d = fmaf(xv.w, acc[3], d);
         }
     } else if (i0 < n) {
 #pragma unroll
@@ -1096,7 +1115,15 @@ static void allow_smem(size_t bytes) {
 // CTAs run on consecutive strips, so the CTAs in flight read one contiguous stretch of
 // each diagonal and of x (DRAM and L2 friendly). Spreading one wave of CTAs over distant
 // equal row ranges instead balances the tail but measured ~10% slower on GB300.
-static int64_t dia_rpt(int vt) { return vt == MSPV_F64 ? 2 : (vt == MSPV_F32 ? 4 : 8); }
+// Rows per thread of the DIA kernels for a value type: the smaller of the FP64-arithmetic and
+// FP32-arithmetic instantiations (the larger grid bounds the CG partial sums).
+static int64_t dia_rpt(int vt) {
+    switch (vt) {
+        case MSPV_F64: return DiaVec<double, double>::RPT;
+        case MSPV_F32: return std::min(DiaVec<float, double>::RPT, DiaVec<float, float>::RPT);
+        default: return std::min(DiaVec<__nv_bfloat16, double>::RPT, DiaVec<__nv_bfloat16, float>::RPT);
+    }
+}
 
 static int64_t csr_grid_for(const mspv_matrix* A);
 
@@ -1122,7 +1149,7 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     if (grid < 1) grid = 1;
     if constexpr (sizeof(T) == 4) {
         launch_kernel(ep.pdl, spmv_dia_f32_kernel<VT>, (unsigned)grid, kThreads, 0, s, A->nrows, A->ndiags,
-                      A->npad, A->doff, static_cast<const VT*>(A->av), x, y, ep);
+                      A->npad, A->doff, (const int2*)A->druns, A->ndruns, static_cast<const VT*>(A->av), x, y, ep);
     } else {
         if (ep.acc)
             launch_kernel(ep.pdl, spmv_dia_kernel<VT, T, true>, (unsigned)grid, kThreads, 0, s, A->nrows,

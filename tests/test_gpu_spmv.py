@@ -306,3 +306,55 @@ def test_memory_cap_injects_enomem(mspv, monkeypatch):
         mspv.Matrix.from_coo(1000, 1000, r, c, v)
     monkeypatch.delenv("MSPV_MAX_BYTES")
     A.convert("csr")   # works again
+
+
+def _fp32_cases():
+    # (name, n, triplet generator): consecutive offsets (runs of 3), isolated offsets (runs of
+    # 1), mixed runs, and a size that is not a multiple of 4 (ragged windows at the ends)
+    return [
+        ("stencil20", 20 ** 3, lambda: synth.stencil27_perturbed(20, 5)),
+        ("banded_isolated", 20001, lambda: synth.banded(20001, 9, 11, 1.0, 3000)),
+        ("banded_mixed", 30003, lambda: synth.banded(30003, 27, 12, 0.9, 40)),
+    ]
+
+
+@pytest.mark.parametrize("case", _fp32_cases(), ids=lambda c: c[0])
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_fp32_arithmetic_spmv(mspv, orc, case, vt, fmt):
+    """The FP32-arithmetic SpMV (the inner SpMV of the FP32 refinement solver) against the
+    oracle on the same rounded values and FP32 x: per row within 2(k+2) u32 sum |a x|, the
+    FP32 counterpart of the FP64 bound (u32 = 2^-24; the products of FP32/BF16 values and FP32
+    x are exact in FP64, only the FP32 sum rounds)."""
+    name, n, gen = case
+    r, c, v = gen()
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    M = A.convert(fmt, vt)
+    O = orc.with_values(orc.convert(orc.canonicalize(n, n, r, c, v), fmt), vt)
+    x32 = (synth.uniform_x(n, 21) * 2 - 1).astype(np.float32)
+    y = M.spmv_f32(dev(x32)).cpu().numpy().astype(np.float64)
+    x64 = x32.astype(np.float64)
+    want = orc.spmv(O, x64)
+    absO = orc.Matrix(O.fmt, O.nrows, O.ncols, O.nnz, ai=O.ai, aj=O.aj, irp=O.irp, av=np.abs(O.av),
+                      doff=O.doff, npad=O.npad)
+    scale = orc.spmv(absO, np.abs(x64))
+    if fmt == "dia":
+        k = np.full(n, O.ndiags)
+    elif fmt == "csr":
+        k = np.diff(O.irp)
+    else:
+        k = np.bincount(O.ai, minlength=n)
+    bound = 2.0 * (k + 2) * 2.0 ** -24 * scale + 1e-30
+    bad = np.nonzero(np.abs(y - want) > bound)[0]
+    assert bad.size == 0, f"{bad.size} rows out of tolerance, first {bad[:5]}"
+
+
+def test_fp32_arithmetic_spmv_rejects_bad_input(mspv):
+    r, c, v = synth.stencil27(6)
+    A = mspv.Matrix.from_coo(216, 216, r, c, v)
+    x = torch.ones(217, dtype=torch.float32, device="cuda")
+    with pytest.raises(mspv.MspvError, match="EFORMAT"):
+        A.convert("dia").spmv_f32(x[:216])
+    D = A.convert("dia", "f32")
+    with pytest.raises(mspv.MspvError, match="EINVAL"):
+        D.spmv_f32(x[1:])   # 4-byte aligned only
