@@ -269,8 +269,8 @@ def run_mspv(args, world, rank, local):
 
     # gpu launches of this library inside the timed region
     coo_launches = 1 + (1 if (nnz + 511) // 512 > 1 else 0)   # segment kernel + carry fix-up
-    # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, r-update, p-update
-    launches_per_step = coo_launches + 1 + 1 + (3 + 4 * args.cg_iters)
+    # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update
+    launches_per_step = coo_launches + 1 + 1 + (3 + 5 * args.cg_iters)
 
     # end to end through the public API with host buffers: every step copies its x and b from
     # pinned host memory and reads the three SpMV results and the CG solution back, all inside

@@ -135,20 +135,38 @@ __global__ void __launch_bounds__(NT) cg_start_kernel(const double* __restrict__
 // alpha = rho / p.q, or a breakdown when p.q <= 0 or alpha is not finite.
 template <int NT>
 __global__ void __launch_bounds__(NT) cg_alpha_kernel(const double* __restrict__ partials, int64_t count,
-                                                            CgState* st, int32_t it) {
+                                                            CgState* st) {
     pdl_wait();
     pdl_trigger();
     if (st->done) return;
     const double pq = sum_partials<NT>(partials, count);
+    if (threadIdx.x == 0) finish_alpha(st, pq);
+}
+
+// rho' = r.r; stop when sqrt(rho') <= tol ||b||; beta = rho' / rho; iteration count.
+template <int NT>
+__global__ void __launch_bounds__(NT) cg_beta_kernel(const double* __restrict__ partials, int64_t count,
+                                                           CgState* st) {
+    pdl_wait();
+    pdl_trigger();
+    if (st->done) return;
+    const double rr = sum_partials<NT>(partials, count);
     if (threadIdx.x == 0) {
-        finish_alpha(st, pq);
-        if (!st->done) {   // the iteration goes on: record it, and rho for the p-update's beta
-            st->rho_prev = st->rho;
-            st->ran = it;
+        st->iters += 1;
+        if (sqrt(rr) <= st->tol * st->bnorm) {
+            st->rho = rr;
+            st->done = 1;
+            st->phase = CG_CONVERGED;
+        } else {
+            st->beta = rr / st->rho;
+            st->rho = rr;
+            if (st->iters >= st->maxit) {
+                st->done = 1;
+                st->phase = CG_MAXIT;
+            }
         }
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // FP64 vector kernels
@@ -191,50 +209,18 @@ __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* 
 }
 
 // p = r + beta p
-// Iteration `it`, after its r-update: every CTA sums the r.r partials itself (the same
-// fixed order everywhere, so every CTA takes the same decisions), forms beta = rho' / rho and
-// the convergence test, then x += alpha p and, unless the iteration converged or reached maxit,
-// p = r + beta p. Thread 0 of CTA 0 records the iteration count, rho' and the stopping state.
-// Only fields no CTA of this kernel writes are read (ran, alpha, rho_prev are set by alpha).
-__device__ __forceinline__ bool cg_step_end(const double* partials, int64_t count, CgState* st, int32_t it,
-                                            double* beta_out) {
-    __shared__ double s_rr;
-    const double tot = sum_partials<kThreads>(partials, count);
-    if (threadIdx.x == 0) s_rr = tot;
-    __syncthreads();
-    const double rr = s_rr;
-    const bool conv = sqrt(rr) <= st->tol * st->bnorm;
-    const double beta = rr / st->rho_prev;
-    const bool last = conv || it >= st->maxit;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->iters = it;
-        st->rho = rr;
-        if (conv) {
-            st->done = 1;
-            st->phase = CG_CONVERGED;
-        } else {
-            st->beta = beta;
-            if (it >= st->maxit) {
-                st->done = 1;
-                st->phase = CG_MAXIT;
-            }
-        }
-    }
-    *beta_out = beta;
-    return !last;
-}
-
+// Iteration `it`: x += alpha p, then p = r + beta p. Runs only when the iteration updated r
+// (its beta kernel counted it: st->iters == it); on the iteration that converged or reached
+// maxit only x is advanced.
 __global__ void __launch_bounds__(kThreads) cg_pupdate_kernel(int64_t n, double* __restrict__ x,
                                                               const double* __restrict__ r,
-                                                              double* __restrict__ p,
-                                                              const double* __restrict__ partials, int64_t count,
-                                                              CgState* st, int32_t it) {
+                                                              double* __restrict__ p, const CgState* st,
+                                                              int32_t it) {
     pdl_wait();
     pdl_trigger();
-    if (st->ran != it) return;
-    double beta;
-    const bool more = cg_step_end(partials, count, st, it, &beta);
-    const double alpha = st->alpha;
+    if (st->iters != it) return;
+    const double alpha = st->alpha, beta = st->beta;
+    const bool more = !st->done;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const double pi = p[i];
         x[i] = fma(alpha, pi, x[i]);
@@ -337,15 +323,19 @@ __global__ void __launch_bounds__(kThreads) cgf_update_kernel(int64_t n, float* 
 
 __global__ void __launch_bounds__(kThreads) cgf_pupdate_kernel(int64_t n, float* __restrict__ x,
                                                                const float* __restrict__ r,
-                                                               float* __restrict__ p,
-                                                               const double* __restrict__ partials, int64_t count,
-                                                               CgState* st, int32_t it) {
+                                                               float* __restrict__ p, const CgState* st,
+                                                               int32_t it) {
     pdl_wait();
     pdl_trigger();
-    if (st->ran != it) return;
-    double beta64;
-    const bool more = cg_step_end(partials, count, st, it, &beta64);
-    const float alpha = (float)st->alpha, beta = (float)beta64;
+    if (st->iters != it) return;
+    __shared__ float s_ab[2];
+    if (threadIdx.x == 0) {
+        s_ab[0] = (float)st->alpha;
+        s_ab[1] = (float)st->beta;
+    }
+    __syncthreads();
+    const float alpha = s_ab[0], beta = s_ab[1];
+    const bool more = !st->done;
     const int64_t n4 = n / 4;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -464,11 +454,11 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
         const int32_t batch = std::min<int32_t>(every, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
-            const int32_t it = launched + k + 1;
-            MSPV_SCALAR_LAUNCH(pdl, cg_alpha_kernel, P, s, (const double*)w.partials, P, w.st, it);
+            MSPV_SCALAR_LAUNCH(pdl, cg_alpha_kernel, P, s, (const double*)w.partials, P, w.st);
             launch_kernel(pdl, update, Gu, kThreads, 0, s, n, r, (const V*)q, w.partials, (const CgState*)w.st);
-            launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, x, (const V*)r, p, (const double*)w.partials,
-                          (int64_t)Gu, w.st, it);
+            MSPV_SCALAR_LAUNCH(pdl, cg_beta_kernel, (int64_t)Gu, s, (const double*)w.partials, (int64_t)Gu, w.st);
+            launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, x, (const V*)r, p, (const CgState*)w.st,
+                          (int32_t)(launched + k + 1));
         }
         MSPV_CUDA_TRY(cudaGetLastError());
         launched += batch;

@@ -117,12 +117,11 @@ struct CgState {
     double beta;
     double bnorm;    // ||b||_2
     double tol;
-    double rho_prev; // rho at the start of the current iteration (read by the p-update kernel)
     int32_t iters;
     int32_t maxit;
     int32_t done;    // nonzero once converged, at maxit, or broken down
     int32_t phase;   // CgPhase
-    int32_t ran;     // the last iteration whose alpha was formed (its r-update runs)
+    uint32_t pad0;
     uint32_t pad1;
 };
 
