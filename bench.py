@@ -41,25 +41,31 @@ NDIAGS = 27
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
 
-# DRAM traffic of one spmv_dia_kernel<double, double> launch without the CG epilogue, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 96^3 stencil; it is scaled
-# to the bench grid by rows (every stream of the kernel grows with n). Reported only while the
-# kernel's source (the DIA section of spmv.cu and its launcher) is the one that was captured.
+# DRAM traffic of one spmv_dia_kernel<double, double, false> launch without the CG epilogue,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 96^3 stencil; it is
+# scaled to the bench grid by rows (every stream of the kernel grows with n). Reported only while
+# the source of that launch (the FP64 value loader, the kernel and the FP64 branch of its
+# launcher) is the one that was captured.
 DIA_TRAFFIC = {"bytes": 201_861_888, "rows": 96 ** 3,
-               "src_sha256": "77987eb3e150fafe90abb1c2769d3e7fe83bf908f485d6b9a47ee3bcb98a58bb"}
+               "src_sha256": "96bba74fbd6d30ed83152b5e581fe7d2aa11c50671dc963507dff5516d55f95a"}
 
 
 def dia_source_sha() -> str | None:
     import hashlib
     try:
         src = open(os.path.join(ROOT, "paper_2304_09511_gb300", "csrc", "spmv.cu")).read()
-        a = src.index("// DIA\n// ---")
-        b = src.index("// FP32-arithmetic DIA")
-        c = src.index("static void launch_dia(")
+        a = src.index("template <> struct DiaVec<double, double> {")
+        b = src.index("\n};\n", a)
+        c = src.index("// One thread per RPT consecutive rows")
         d = src.index("\n}\n", c)
+        e = src.index("static void launch_dia(")
+        f = src.index("\n}\n", e)
+        body = src[e:f]
+        i = body.index("if constexpr (sizeof(T) == 4) {")
+        j = body.index("} else {", i)
     except (OSError, ValueError):
         return None
-    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()
+    return hashlib.sha256((src[a:b] + src[c:d] + body[:i] + body[j:]).encode()).hexdigest()
 
 
 def dia_traffic(n: int) -> int | None:

@@ -2,14 +2,14 @@
 // with the preconditioner disabled (Sec. VI), and an FP64 iterative-refinement loop
 // around it for low-precision matrix values (not in the paper).
 //
-// One iteration is five kernels on the caller's stream, none of which waits on the
-// host or on another CTA:
+// One iteration is five kernels on the caller's stream, chained by programmatic dependent
+// launches; none of them waits on the host or on another CTA:
 //   1. q = A p; each CTA also writes its partial sum of p.q;
-//   2. (one CTA) p.q = sum of the partials in index order; alpha = rho / p.q, or a
+//   2. (one CTA) p.q = sum of the partials in a fixed order; alpha = rho / p.q, or a
 //      breakdown;
-//   3. x += alpha p, r -= alpha q; each CTA writes its partial of r.r;
+//   3. r -= alpha q; each CTA writes its partial of r.r;
 //   4. (one CTA) rho' = r.r; convergence test, iteration count, beta = rho' / rho;
-//   5. p = r + beta p.
+//   5. x += alpha p, then p = r + beta p (one pass over p).
 // Every scalar lives in a device CgState. Once `done` is set all kernels return at
 // entry, so the host may launch past convergence and polls the state only every
 // MSPV_CG_CHECK_EVERY iterations. Reductions are deterministic (fixed order) and use

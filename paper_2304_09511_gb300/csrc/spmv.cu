@@ -1,31 +1,35 @@
-// SpMV kernels for the three storage formats of Sec. II-B, y = A x, FP64 arithmetic.
+// SpMV kernels for the three storage formats of Sec. II-B, y = A x (or y += A x), FP64
+// arithmetic, plus the FP32-arithmetic kernels of the refinement's inner solver.
 //
 // On GB300 the FP64 pipe, not HBM, is the tighter limit for FP64 SpMV: one FP64 FMA
 // per stored value is about as fast as HBM delivers that value, a warp instruction
 // costs the same however many of its lanes are active, and the FP32 -> FP64
 // conversion instruction issues on the same narrow pipe. Every kernel here therefore
-// spends exactly one lane-dense FMA per value it must multiply, widens FP32/BF16
-// values with integer instructions, and avoids FP64 shuffle reductions.
+// spends one FMA per value it must multiply with as many lanes busy as it can, widens
+// FP32/BF16 values with integer instructions, and keeps FP64 shuffle reductions short.
 //
 //  DIA (Algorithm 3): diagonal-major values; each thread owns RPT consecutive rows
-//      (FP64: 2, FP32: 4, BF16: 8, one 128-bit value load per diagonal) and walks the
-//      diagonals in order with the predicate 0 <= k < N -- the row-parallel,
-//      diagonal-sequential structure of the paper's outer-loop SVE vectorisation
-//      (Sec. III), with the lanes of a warp in place of SVE lanes.
-//  CSR (Algorithm 2): a CTA takes the rows that start in a window of ~2560 entries,
-//      stages their values and gathered x[aj] through shared memory with coalesced,
-//      independent loads, then each thread sums one row left to right with FMAs.
-//      Rows longer than 128 entries are reduced by the whole CTA. A V-lanes-per-row
-//      kernel (V = 1..32, warp per row at V = 32) is kept for very long rows.
-//  COO (Algorithm 1): a CTA takes a window of 3072 sorted entries, stages them, finds
-//      the runs of equal row index with a block scan, and sums each run in one
-//      thread -- the segmented reduction over runs of equal row index that the
-//      paper's SVE COO kernel performs with a match mask and a horizontal add. Runs
-//      cut by a window edge leave partial sums in a carry record that a fix-up pass
-//      adds in window order.
-// No floating-point atomics anywhere: y is bit-identical run to run. Each kernel can
-// fuse CG's p.q into its epilogue (DotEpilogue); the last CTA reduces the per-CTA
-// partials in index order and forms alpha.
+//      (FP64 arithmetic: 2 rows for FP64 values, 4 for FP32, 8 for BF16, one 128-bit
+//      value load per diagonal) and walks the diagonals in order with the predicate
+//      0 <= k < N -- the row-parallel, diagonal-sequential structure of the paper's
+//      outer-loop SVE vectorisation (Sec. III), with warp lanes in place of SVE lanes.
+//      The FP32-arithmetic kernel reads one x window per run of consecutive offsets.
+//  CSR (Algorithm 2): V lanes per row (V = 4 for short rows, chosen from the row-length
+//      statistics), lane-strided FMAs and a log2(V)-step shuffle reduction; rows longer
+//      than 32 V entries are listed at conversion and reduced by one CTA each. Inside CG
+//      the grid is capped and the row groups stride. Kernels that stage values and
+//      gathered x through shared memory (warp slices, CTA row blocks) are selectable.
+//  COO (Algorithm 1): rows of at most 128 entries take the run-vector kernel (a warp per
+//      256 sorted entries: ballot-compacted run starts, then 4 lanes per run); longer
+//      rows the lane-sequential segment kernel (16 entries per lane summed in order, a
+//      segmented scan joins rows across lanes) -- both forms of the paper's SVE COO idea
+//      of reducing runs of equal row index. Runs cut by a chunk edge leave partial sums in
+//      a carry record that a fix-up pass adds in chunk order. A staged window kernel
+//      serves the allocation-free entry point.
+// No floating-point atomics anywhere: y is bit-identical run to run. Inside CG each
+// SpMV kernel writes its CTA's partial of p.q (DotEpilogue); the partials are summed in
+// index order by a one-CTA kernel. store_y is the single place a row of y is written
+// (overwrite, or add for the accumulating SpMV).
 #include <algorithm>
 #include <climits>
 #include <cstdlib>
