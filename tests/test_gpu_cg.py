@@ -193,3 +193,42 @@ def test_cg_with_an_unaligned_solution_vector(mspv, stencil16):
     r2 = D.cg(b, tol=0.0, maxit=15)
     assert r1.iters == r2.iters == 15
     assert torch.equal(r1.x, r2.x)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "coo"])
+@pytest.mark.parametrize("mean_len", [6, 60])
+def test_cg_with_long_rows_matches_oracle(mspv, orc, fmt, mean_len):
+    """SPD matrices whose CSR form lists long rows (a few dense rows and columns) and whose
+    mean row length selects V = 4 or V = 8: inside CG the V-lane kernel runs on a capped grid
+    and the long-row kernel writes its p.q partials after it; COO takes the segment kernel.
+    Fixed iterations track the oracle's iterates."""
+    rng = np.random.default_rng(mean_len)
+    n = 200_000
+    m = n * mean_len // 2
+    r = rng.integers(0, n, m)
+    c = rng.integers(0, n, m)
+    hubs = rng.choice(n, 6, replace=False)
+    hr = np.repeat(hubs, 3000)
+    hc = rng.integers(0, n, hr.size)
+    r = np.concatenate([r, hr])
+    c = np.concatenate([c, hc])
+    keep = r != c
+    r, c = r[keep], c[keep]
+    v = -rng.uniform(0.1, 1.0, r.size)
+    rows = np.concatenate([r, c, np.arange(n)])          # symmetric off-diagonal part
+    cols = np.concatenate([c, r, np.arange(n)])
+    absrow = np.bincount(np.concatenate([r, c]), weights=np.abs(np.concatenate([v, v])), minlength=n)
+    vals = np.concatenate([v, v, absrow + 1.0])           # strictly diagonally dominant
+    A = mspv.Matrix.from_coo(n, n, dev(rows.astype(np.int32)), dev(cols.astype(np.int32)), dev(vals))
+    M = A if fmt == "coo" else A.convert(fmt)
+    if fmt == "csr":
+        info = M.info
+        assert info["csr_vector"] == (4 if mean_len < 48 else 8) and info["row_max"] > 32 * info["csr_vector"]
+    O = orc.convert(orc.canonicalize(n, n, rows, cols, vals), fmt)
+    b = synth.uniform_x(n, 3)
+    for k in (3, 12):
+        res = M.cg(dev(b), tol=0.0, maxit=k)
+        xo, st, ko, rel, _, _ = orc.cg(O, b, tol=0.0, maxit=k)
+        assert res.iters == k == ko
+        assert np.max(np.abs(res.x.cpu().numpy() - xo)) <= 1e-11 * np.max(np.abs(xo))
+        assert res.relres == pytest.approx(rel, rel=1e-8)
