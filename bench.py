@@ -362,6 +362,9 @@ def run_mspv(args, world, rank, local):
                                                         max_outer=30, maxit_inner=5000, inner_fp32=True)),
         ("ir_bf16_values_fp32_inner", lambda xx: D.cg_ir(D16, b, x=xx, tol=1e-10, inner_tol=args.ir_inner_tol,
                                                          max_outer=30, maxit_inner=5000, inner_fp32=True)),
+        # one FP32-arithmetic CG with reliable FP64 residual updates
+        ("ru_f32_values", lambda xx: D.cg_ru(D32, b, x=xx, tol=1e-10, maxit=5000)),
+        ("ru_bf16_values", lambda xx: D.cg_ru(D16, b, x=xx, tol=1e-10, maxit=5000)),
     )
     for label, fn in modes:
         os.environ["MSPV_CG_CHECK_EVERY"] = "10"
@@ -567,6 +570,8 @@ def _selector_stencil_e2e(mspv, torch, dev, params, g):
         res["ir_f32_values_fp32_inner_selector_format"] = timed(
             lambda xx: M64[pick].cg_ir(Mlo, b, x=xx, tol=1e-10, inner_tol=1e-6, max_outer=30,
                                        maxit_inner=20000, inner_fp32=True))
+        res["ru_f32_values_selector_format"] = timed(
+            lambda xx: M64[pick].cg_ru(Mlo, b, x=xx, tol=1e-10, maxit=20000))
     return res
 
 
@@ -629,13 +634,22 @@ def run_mixed(args, world, rank, local):
             out[f"ir_{vt}_values_fp32_inner"] = timed(
                 lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=args.ir_inner_tol, max_outer=30,
                                    maxit_inner=20000, inner_fp32=True))
+            out[f"ru_{vt}_values"] = timed(lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, maxit=20000))
             L.close()
-        if fmt == "dia":   # inner tolerance of the FP32-arithmetic solver (BF16 values)
+        if fmt == "dia":   # inner tolerance of the restarted solver, update threshold of the reliable one
             L = A.convert(fmt, "bf16")
             for itol in (1e-3, 1e-4, 1e-5, 1e-7):
                 out[f"ir_bf16_values_fp32_inner_tol{itol:g}"] = timed(
                     lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=itol, max_outer=40, maxit_inner=20000,
                                        inner_fp32=True))
+            for d in (0.03, 0.3):
+                out[f"ru_bf16_values_delta{d:g}"] = timed(
+                    lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, delta=d, max_updates=200, maxit=20000))
+            L.close()
+            L = A.convert(fmt, "f32")
+            for d in (1e-3, 1e-1):
+                out[f"ru_f32_values_delta{d:g}"] = timed(
+                    lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, delta=d, max_updates=200, maxit=20000))
             L.close()
         M.close()
         results[fmt] = out
@@ -645,8 +659,9 @@ def run_mixed(args, world, rank, local):
            "n_gpus": world, "mode": "mixed", "scaling": "weak", "data": "synthetic",
            "dtype": "f64 outer; f32/bf16 values", "best": {"format": best[1], "solver": best[2]},
            "config": {"workload": f"27-point stencil {g}^3 (n={n}, nnz={nnz}), b = A 1, x0 = 0, to 1e-10 "
-                                  "relative residual; CSR and DIA; FP64 CG vs FP64-outer refinement with "
-                                  "FP32 or BF16 stored values", "parallelism": f"replicas x{world}"},
+                                  "relative residual; CSR and DIA; FP64 CG vs FP64-outer refinement "
+                                  "(restarted, or one FP32 CG with reliable updates) with FP32 or BF16 "
+                                  "stored values", "parallelism": f"replicas x{world}"},
            "results": results, "clocks": clk}
     if world > 1:
         torch.distributed.destroy_process_group()

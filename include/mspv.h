@@ -156,6 +156,18 @@ MSPV_API mspv_status mspv_cg_solve(mspv_matrix_t A, const double* b, double* x, 
  *   every dot product kept in FP64; x += ||r|| d in FP64. Alo must store FP32 or BF16
  *   values (EFORMAT otherwise). On GB300, whose FP64 pipe is ~1/64 of its FP32 pipe,
  *   this is the mode that makes refinement faster than plain FP64 CG.
+ * inner_fp32 = 2: reliable updates instead of restarts. One FP32-arithmetic CG on Alo
+ *   (scalars in FP64, as for 1) runs throughout and accumulates a correction y; x and
+ *   the residual stay in FP64. When its recursive residual has fallen by the factor
+ *   inner_tol since the last update, or to tol ||b||, the update does x += y, r = b -
+ *   A64 x in FP64, stops when ||r|| / ||b|| <= tol, and otherwise continues the same CG
+ *   from the replaced residual with p = r + beta p, beta = ||r||^2 / (r.r before the
+ *   last iteration), so the search direction is kept (Sleijpen and van der Vorst's
+ *   reliable updated residuals). inner_tol <= 0 selects 1e-2 for FP32 values and 1e-1
+ *   for BF16 values. max_outer bounds the updates and maxit_inner the total FP32
+ *   iterations; *outer_iters returns the updates and *inner_iters the FP32 iterations.
+ *   With FP32 values this needs about as many iterations as FP64 CG.
+ * inner_fp32 outside 0..2 is EINVAL.
  * Outputs (host, may be NULL): *outer_iters, *inner_iters (sum over corrections),
  * *relres = final ||b - A64 x|| / ||b||. Returns OK, ENOTCONV or EBREAKDOWN.
  */

@@ -15,6 +15,9 @@ Functions and the passages they follow:
   cg             unpreconditioned CG as run in the paper's HPCG experiments (Sec. VI)
   cg_ir          FP64 iterative refinement around a low-precision inner CG (not in
                  the paper; pinned only by its final FP64 residual)
+  cg_ru          one low-precision CG with reliable updates of its residual from
+                 FP64 (not in the paper; pinned by finite termination, by equality
+                 with cg when both matrices are equal, and by its final residual)
 """
 from __future__ import annotations
 
@@ -76,6 +79,7 @@ def _L():
             "orc_round_values": (None, [i64, vp, i32, vp]),
             "orc_cg": (i32, [vp, vp, vp, dbl, i32, vp, vp, vp, vp, vp]),
             "orc_cg_ir": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, vp, vp]),
+            "orc_cg_ru": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -245,3 +249,19 @@ def cg_ir(A64: Matrix, Alo: Matrix, b, x0=None, tol=1e-10, inner_tol=1e-6, max_o
                         inner_tol, max_outer, maxit_inner, ctypes.addressof(oi),
                         ctypes.addressof(ii), ctypes.addressof(rr))
     return x, st, oi.value, ii.value, rr.value
+
+
+def cg_ru(A64: Matrix, Alo: Matrix, b, x0=None, tol=1e-10, delta=1e-2, max_updates=100,
+          maxit=10000):
+    """Returns (x, status, updates, iters, relres)."""
+    n = A64.nrows
+    b = _f64(b)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    nu = ctypes.c_int32(0)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    m64, mlo = A64._struct(), Alo._struct()
+    st = _L().orc_cg_ru(ctypes.addressof(m64), ctypes.addressof(mlo), _p(b), _p(x), tol, delta,
+                        max_updates, maxit, ctypes.addressof(nu),
+                        ctypes.addressof(it), ctypes.addressof(rr))
+    return x, st, nu.value, it.value, rr.value

@@ -36,6 +36,12 @@
  *                         low-precision matrix. Not in the paper: parity
  *                         unpinned against the paper, pinned by its final FP64
  *                         residual only.
+ *   orc_cg_ru             one CG on the low-precision matrix whose residual is
+ *                         replaced by the true FP64 residual b - A64 x at
+ *                         "reliable updates" (Sleijpen and van der Vorst). Not in
+ *                         the paper: pinned by finite termination, by reducing
+ *                         to orc_cg when both matrices are equal and by its
+ *                         final FP64 residual.
  */
 #include <math.h>
 #include <stdint.h>
@@ -357,5 +363,78 @@ int32_t orc_cg_ir(const orc_matrix* A64, const orc_matrix* Alo, const double* b,
     }
 done:
     free(r); free(d);
+    return status;
+}
+
+/* Reliable updates (not in the paper). One CG runs on Alo throughout; x stays in
+ * FP64 and the low-precision iteration accumulates its correction y:
+ *   x from x0; r = b - A64 x; stop at once when ||r|| <= tol ||b||;
+ *   y = 0; p = r; rho = r.r; rlast = ||r||
+ *   per iteration: q = Alo p; alpha = rho / (p.q); y += alpha p; r -= alpha q;
+ *     an update is due when ||r|| <= delta * rlast, ||r|| <= tol ||b|| or the
+ *     iteration count reaches maxit; it does x += y; y = 0; r = b - A64 x;
+ *     rlast = ||r||, and stops when ||r|| <= tol ||b|| (OK) or after max_updates
+ *     updates or maxit iterations (NOTCONV);
+ *     then (r being the recursive or the replaced residual)
+ *     beta = r.r / rho; rho = r.r; p = r + beta p.
+ * p.q <= 0 or a non-finite alpha is a breakdown (x then holds the last update).
+ * updates counts the updates done; iters the iterations on Alo. */
+int32_t orc_cg_ru(const orc_matrix* A64, const orc_matrix* Alo, const double* b, double* x,
+                  double tol, double delta, int32_t max_updates, int32_t maxit,
+                  int32_t* updates, int32_t* iters, double* relres) {
+    int32_t n = A64->nrows;
+    size_t sz = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double* r = (double*)malloc(sz);
+    double* p = (double*)malloc(sz);
+    double* q = (double*)malloc(sz);
+    double* y = (double*)malloc(sz);
+    int32_t status = ORC_NOTCONV;
+    int32_t k = 0;
+    *updates = 0;
+    *iters = 0;
+    *relres = 0.0;
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        for (int32_t i = 0; i < n; i++) x[i] = 0.0;
+        status = ORC_OK;
+        goto done;
+    }
+    matvec(A64, x, q);
+    for (int32_t i = 0; i < n; i++) r[i] = b[i] - q[i];
+    double rho = dot(n, r, r);
+    double rlast = sqrt(rho);
+    *relres = rlast / bnorm;
+    if (rlast <= tol * bnorm) { status = ORC_OK; goto done; }
+    for (int32_t i = 0; i < n; i++) { p[i] = r[i]; y[i] = 0.0; }
+    for (;;) {
+        if (k < maxit) {
+            matvec(Alo, p, q);
+            double pq = dot(n, p, q);
+            double alpha = rho / pq;
+            if (!(pq > 0.0) || !isfinite(alpha)) { status = ORC_BREAKDOWN; break; }
+            for (int32_t i = 0; i < n; i++) y[i] = y[i] + alpha * p[i];
+            for (int32_t i = 0; i < n; i++) r[i] = r[i] - alpha * q[i];
+            k++;
+        }
+        double rr = dot(n, r, r);
+        double rn = sqrt(rr);
+        if (rn <= delta * rlast || rn <= tol * bnorm || k >= maxit) {
+            for (int32_t i = 0; i < n; i++) { x[i] = x[i] + y[i]; y[i] = 0.0; }
+            matvec(A64, x, q);
+            for (int32_t i = 0; i < n; i++) r[i] = b[i] - q[i];
+            rr = dot(n, r, r);
+            rlast = sqrt(rr);
+            *updates += 1;
+            *relres = rlast / bnorm;
+            if (rlast <= tol * bnorm) { status = ORC_OK; break; }
+            if (*updates >= max_updates || k >= maxit) { status = ORC_NOTCONV; break; }
+        }
+        double beta = rr / rho;
+        rho = rr;
+        for (int32_t i = 0; i < n; i++) p[i] = r[i] + beta * p[i];
+    }
+    *iters = k;
+done:
+    free(r); free(p); free(q); free(y);
     return status;
 }

@@ -238,10 +238,11 @@ class Matrix:
         return _FMT_NAMES[best.value]
 
     def cg_ir(self, low: "Matrix", b, x=None, tol: float = 1e-10, inner_tol: float = 1e-6,
-              max_outer: int = 50, maxit_inner: int = 10000, inner_fp32: bool = False,
+              max_outer: int = 50, maxit_inner: int = 10000, inner_fp32: int = 0,
               stream=None) -> CgResult:
         """Iterative refinement: FP64 residuals on self, inner CG on `low` (e.g. BF16 values),
-        in FP64 arithmetic or (inner_fp32=True) in FP32 arithmetic."""
+        in FP64 arithmetic (inner_fp32=0), in FP32 arithmetic (1), or one FP32 CG with
+        reliable updates (2; see cg_ru)."""
         import torch
         n = self.shape[0]
         _check_vec(b, n)
@@ -250,11 +251,20 @@ class Matrix:
         _check_vec(x, n)
         oi, ii, rr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
         st = load().mspv_cg_solve_ir(self._h, low._h, b.data_ptr(), x.data_ptr(), float(tol),
-                                     float(inner_tol), int(max_outer), int(maxit_inner), int(bool(inner_fp32)),
+                                     float(inner_tol), int(max_outer), int(maxit_inner), int(inner_fp32),
                                      stream_handle(stream), ctypes.byref(oi), ctypes.byref(ii),
                                      ctypes.byref(rr))
         _lib.check(st, allow=(_lib.ENOTCONV, _lib.EBREAKDOWN))
         return CgResult(x, st, ii.value, rr.value, outer_iters=oi.value)
+
+    def cg_ru(self, low: "Matrix", b, x=None, tol: float = 1e-10, delta: float = 0.0,
+              max_updates: int = 100, maxit: int = 10000, stream=None) -> CgResult:
+        """Mixed precision with reliable updates: one FP32 CG on `low` (FP32 or BF16 values)
+        whose residual is replaced by the FP64 residual of self when it has fallen by `delta`
+        (0 = the library's default for the value type). iters counts FP32 iterations and
+        outer_iters the updates."""
+        return self.cg_ir(low, b, x, tol=tol, inner_tol=delta, max_outer=max_updates, maxit_inner=maxit,
+                          inner_fp32=2, stream=stream)
 
 
 def _params_array(params) -> np.ndarray:

@@ -1,6 +1,8 @@
 // Unpreconditioned conjugate gradient, the solver the paper's HPCG experiments run
-// with the preconditioner disabled (Sec. VI), and an FP64 iterative-refinement loop
-// around it for low-precision matrix values (not in the paper).
+// with the preconditioner disabled (Sec. VI), and two mixed-precision solvers for
+// low-precision matrix values (not in the paper): FP64 iterative refinement around a
+// restarted inner CG, and one FP32 CG whose residual is replaced by the FP64 one at
+// reliable updates.
 //
 // One iteration is five kernels on the caller's stream, chained by programmatic dependent
 // launches; none of them waits on the host or on another CTA:
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(NT) cg_beta_kernel(const double* __restrict__ 
     if (threadIdx.x == 0) {
         st->iters += 1;
         if (sqrt(rr) <= st->tol * st->bnorm) {
+            st->rho_prev = st->rho;
             st->rho = rr;
             st->done = 1;
             st->phase = CG_CONVERGED;
@@ -189,7 +192,6 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(int64_t n, const doub
     write_partial(bb, pbb);
 }
 
-// x += alpha p; r -= alpha q; partial of r.r.
 // r -= alpha q with the CTA partial of r.r. x is advanced by the p-update kernel, which reads
 // p anyway (x += alpha p there saves one pass over p per iteration).
 __global__ void __launch_bounds__(kThreads) cg_update_kernel(int64_t n, double* __restrict__ r,
@@ -372,6 +374,25 @@ __global__ void ir_correct_kernel(int64_t n, double* __restrict__ x, double scal
         x[i] = fma(scale, f32_to_f64(d32[i]), x[i]);
 }
 
+// Reliable-update glue: x += sigma * (double)y32 and y32 = 0 (the FP32 correction folded
+// into the FP64 solution); r32 = (float)(r / sigma') with p32 = r32 + c p32 (c = 0: p32 = r32),
+// the replaced residual in its new unit and the direction formed from it.
+__global__ void ru_fold_kernel(int64_t n, double* __restrict__ x, double sigma, float* __restrict__ y32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fma(sigma, f32_to_f64(y32[i]), x[i]);
+        y32[i] = 0.0f;
+    }
+}
+
+__global__ void ru_restart_kernel(int64_t n, const double* __restrict__ r, double inv_sigma,
+                                  float* __restrict__ r32, float* __restrict__ p32, float c) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float ri = __double2float_rn(r[i] * inv_sigma);
+        r32[i] = ri;
+        p32[i] = c == 0.0f ? ri : fmaf(c, p32[i], ri);
+    }
+}
+
 __global__ void zero_f32_kernel(float* __restrict__ v, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = 0.0f;
@@ -438,11 +459,12 @@ static int check_every() {
 // vector type, Spmv(x, y, ep) launches the SpMV with its p.q partials.
 template <typename V, typename SpmvFn, typename UpdateK, typename PupdateK>
 static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t maxit, cudaStream_t s,
-                              SpmvFn spmv, UpdateK update, PupdateK pupdate, unsigned Gu, unsigned Gp) {
+                              SpmvFn spmv, UpdateK update, PupdateK pupdate, unsigned Gu, unsigned Gp,
+                              int32_t it0 = 0) {
     CgWork& w = A->cg;
     CgState* hst = w.host_st;
     const int64_t n = A->nrows;
-    const int64_t P = spmv_partials_needed(A);
+    const int64_t P = spmv_partials_count(A, sizeof(V) == sizeof(float));   // exactly the partials the SpMV writes
     const bool pdl = use_pdl();
     const DotEpilogue ep{w.st, w.partials, pdl};
     const int every = check_every();
@@ -458,7 +480,7 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
             launch_kernel(pdl, update, Gu, kThreads, 0, s, n, r, (const V*)q, w.partials, (const CgState*)w.st);
             MSPV_SCALAR_LAUNCH(pdl, cg_beta_kernel, (int64_t)Gu, s, (const double*)w.partials, (int64_t)Gu, w.st);
             launch_kernel(pdl, pupdate, Gp, kThreads, 0, s, n, x, (const V*)r, p, (const CgState*)w.st,
-                          (int32_t)(launched + k + 1));
+                          (int32_t)(it0 + launched + k + 1));
         }
         MSPV_CUDA_TRY(cudaGetLastError());
         launched += batch;
@@ -551,6 +573,111 @@ static mspv_status cg_solve_f32(mspv_matrix* A, const float* b32, float* x32, do
     return MSPV_OK;
 }
 
+// Mixed precision with reliable updates (inner_fp32 = 2). One FP32-arithmetic CG on Alo runs
+// throughout, on the residual in units of sigma (its FP64 norm at the last update), and
+// accumulates its correction y32. The FP32 iteration stops itself, on the device, in the
+// iteration where its recursive residual falls below delta (relative to the last update) or to
+// the FP64 target; the update then folds sigma y32 into the FP64 x, recomputes the true
+// residual b - A64 x in FP64, stops once it meets tol, and otherwise restarts the FP32
+// iteration on the replaced residual in its new unit sigma' with the direction
+//     p = r' + beta p,   beta = ||r'||^2 / rho_prev   (in the new unit: sigma' / (sigma rho_prev)),
+// so the search direction, and with it the Krylov space, survives the update (reliable
+// updated residuals, Sleijpen and van der Vorst). inner_tol <= 0 takes delta = 1e-2 for FP32
+// values and 1e-1 for BF16 values, whose larger rounding of A needs more frequent updates.
+static mspv_status cg_solve_ru(mspv_matrix* A64, mspv_matrix* Alo, const double* b, double* x, double tol,
+                               double delta, int32_t max_updates, int32_t maxit, cudaStream_t s,
+                               int32_t* updates, int32_t* iters, double* relres) {
+    const int64_t n = A64->nrows;
+    if (!(delta > 0.0)) delta = Alo->value_type == MSPV_BF16 ? 1e-1 : 1e-2;
+    MSPV_TRY(ensure_cg_work(A64));
+    MSPV_TRY(ensure_cg_work_f32(Alo));
+    DevBuf rbuf, qbuf, ybuf;
+    MSPV_TRY(rbuf.alloc(sizeof(double) * n));
+    MSPV_TRY(qbuf.alloc(sizeof(double) * n));
+    MSPV_TRY(ybuf.alloc(sizeof(float) * n));
+    double* r = rbuf.as<double>();
+    double* q = qbuf.as<double>();
+    float* y32 = ybuf.as<float>();
+    CgState* ost = A64->cg.st + 1;
+    CgState* host = A64->cg.host_st + 1;
+    *host = CgState{};
+    MSPV_CUDA_TRY(cudaMemcpyAsync(ost, host, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    const unsigned G = (unsigned)vec_grid(n);
+    const int64_t half = A64->cg.npartials / 2;
+    auto true_residual = [&]() -> mspv_status {   // r = b - A64 x with ||r||, ||b|| in FP64
+        MSPV_TRY(launch_spmv(A64, x, q, s, DotEpilogue{nullptr, nullptr}));
+        ir_residual_kernel<<<G, kThreads, 0, s>>>(n, b, q, r, A64->cg.partials, A64->cg.partials + half);
+        MSPV_SCALAR_LAUNCH(false, ir_norms_kernel, (int64_t)G, s, (const double*)A64->cg.partials,
+                           (const double*)(A64->cg.partials + half), (int64_t)G, ost);
+        MSPV_CUDA_TRY(cudaGetLastError());
+        MSPV_CUDA_TRY(cudaMemcpyAsync(host, ost, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        return MSPV_OK;
+    };
+    MSPV_TRY(true_residual());
+    if (host->bnorm == 0.0) {
+        zero_kernel<<<G, kThreads, 0, s>>>(x, n);
+        MSPV_CUDA_TRY(cudaGetLastError());
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        return MSPV_OK;
+    }
+    const double bnorm = host->bnorm;
+    double sigma = std::sqrt(host->rho);
+    if (relres) *relres = sigma / bnorm;
+    if (sigma <= tol * bnorm) return MSPV_OK;
+
+    CgWork& w = Alo->cg;
+    CgState* hst = w.host_st;
+    const unsigned Gu = (unsigned)wave_grid<cgf_update_kernel>(n);
+    const unsigned Gp = (unsigned)wave_grid<cgf_pupdate_kernel>(n);
+    ru_restart_kernel<<<G, kThreads, 0, s>>>(n, r, 1.0 / sigma, w.rf, w.pf, 0.0f);
+    zero_f32_kernel<<<G, kThreads, 0, s>>>(y32, n);
+    *hst = CgState{};
+    hst->maxit = maxit;
+    hst->bnorm = 1.0;   // the FP32 residual is measured in units of sigma
+    int32_t done = 0, nupd = 0;
+    mspv_status result = MSPV_ENOTCONV;
+    for (;;) {
+        // restart the FP32 iteration on r / sigma (unit norm); it stops below its threshold
+        hst->rho = 1.0;
+        hst->tol = std::max(delta, tol * bnorm / sigma);
+        hst->done = 0;
+        hst->phase = CG_RUNNING;
+        MSPV_CUDA_TRY(cudaMemcpyAsync(w.st, hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
+        if (done < maxit)
+            MSPV_TRY(cg_iterate(
+                Alo, y32, w.rf, w.pf, w.qf, maxit - done, s,
+                [&](const float* pp, float* qq, DotEpilogue ep) { return launch_spmv_f32(Alo, pp, qq, s, ep); },
+                cgf_update_kernel, cgf_pupdate_kernel, Gu, Gp, done));
+        if (hst->phase == CG_BREAKDOWN) {
+            result = set_error(MSPV_EBREAKDOWN, "cg (reliable updates): breakdown at FP32 iteration %d", hst->iters);
+            break;
+        }
+        done = hst->iters;
+        // reliable update: fold the correction into x and replace the residual by the true one
+        ru_fold_kernel<<<G, kThreads, 0, s>>>(n, x, sigma, y32);
+        MSPV_TRY(true_residual());
+        ++nupd;
+        const double sigma_new = std::sqrt(host->rho);
+        if (relres) *relres = sigma_new / bnorm;
+        if (sigma_new <= tol * bnorm) { result = MSPV_OK; break; }
+        if (nupd >= max_updates || done >= maxit) break;
+        const double c = sigma_new / (sigma * hst->rho_prev);
+        ru_restart_kernel<<<G, kThreads, 0, s>>>(n, r, 1.0 / sigma_new, w.rf, w.pf, (float)c);
+        sigma = sigma_new;
+    }
+    if (updates) *updates = nupd;
+    if (iters) *iters = done;
+    MSPV_CUDA_TRY(cudaGetLastError());
+    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (result == MSPV_ENOTCONV)
+        return set_error(MSPV_ENOTCONV, "cg (reliable updates): %d FP32 iterations, %d updates, residual %g above %g",
+                         done, nupd, relres ? *relres : 0.0, tol);
+    if (result != MSPV_OK) return result;
+    clear_error();
+    return MSPV_OK;
+}
+
 mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, double* x,
                         double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
                         int32_t inner_fp32, cudaStream_t s, int32_t* outer_iters,
@@ -558,6 +685,7 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
     if (A64->nrows != A64->ncols || Alo->nrows != A64->nrows || Alo->ncols != A64->ncols)
         return set_error(MSPV_EFORMAT, "cg_ir: matrices must be square and of equal size");
     if (max_outer < 0 || maxit_inner < 0) return set_error(MSPV_EINVAL, "cg_ir: negative iteration limit");
+    if (inner_fp32 < 0 || inner_fp32 > 2) return set_error(MSPV_EINVAL, "cg_ir: inner_fp32 = %d", inner_fp32);
     if (inner_fp32 && Alo->value_type == MSPV_F64)
         return set_error(MSPV_EFORMAT, "cg_ir: FP32 inner arithmetic needs FP32 or BF16 values in Alo");
     const int64_t n = A64->nrows;
@@ -565,6 +693,9 @@ mspv_status cg_solve_ir(mspv_matrix* A64, mspv_matrix* Alo, const double* b, dou
     if (inner_iters) *inner_iters = 0;
     if (relres) *relres = 0.0;
     if (n == 0) return MSPV_OK;
+    if (inner_fp32 == 2)
+        return cg_solve_ru(A64, Alo, b, x, tol, inner_tol, max_outer, maxit_inner, s, outer_iters, inner_iters,
+                           relres);
     MSPV_TRY(ensure_cg_work(A64));
     // outer vectors are separate buffers so that Alo may be the same handle as A64
     DevBuf rbuf, dbuf, qbuf, r32buf, d32buf;

@@ -121,8 +121,8 @@ struct CgState {
     int32_t maxit;
     int32_t done;    // nonzero once converged, at maxit, or broken down
     int32_t phase;   // CgPhase
-    uint32_t pad0;
-    uint32_t pad1;
+    double rho_prev; // r.r before the iteration that converged (reliable updates form the
+                     // next direction from it)
 };
 
 // An SpMV kernel's optional epilogue for CG: each CTA writes its partial of the dot x.y
@@ -281,7 +281,8 @@ mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaSt
 // mixed-precision refinement. EFORMAT for FP64 stored values.
 mspv_status launch_spmv_f32(const mspv_matrix* A, const float* x, float* y, cudaStream_t s,
                             DotEpilogue ep);
-int64_t spmv_partials_needed(const mspv_matrix* A);   // CTAs of the fused-dot launch
+int64_t spmv_partials_count(const mspv_matrix* A, bool f32);   // CTAs of the fused-dot launch
+int64_t spmv_partials_needed(const mspv_matrix* A);   // the larger of the FP64 and FP32 counts
 mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* aj,
                            const double* av, const double* x, double* y, CooCarry* carry,
                            cudaStream_t s);

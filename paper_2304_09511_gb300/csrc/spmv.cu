@@ -1119,22 +1119,24 @@ static void allow_smem(size_t bytes) {
 // CTAs run on consecutive strips, so the CTAs in flight read one contiguous stretch of
 // each diagonal and of x (DRAM and L2 friendly). Spreading one wave of CTAs over distant
 // equal row ranges instead balances the tail but measured ~10% slower on GB300.
-// Rows per thread of the DIA kernels for a value type: the smaller of the FP64-arithmetic and
-// FP32-arithmetic instantiations (the larger grid bounds the CG partial sums).
-static int64_t dia_rpt(int vt) {
+// Rows per thread of the DIA kernel that a value type and arithmetic launch.
+static int64_t dia_rpt(int vt, bool f32) {
     switch (vt) {
         case MSPV_F64: return DiaVec<double, double>::RPT;
-        case MSPV_F32: return std::min(DiaVec<float, double>::RPT, DiaVec<float, float>::RPT);
-        default: return std::min(DiaVec<__nv_bfloat16, double>::RPT, DiaVec<__nv_bfloat16, float>::RPT);
+        case MSPV_F32: return f32 ? DiaVec<float, float>::RPT : DiaVec<float, double>::RPT;
+        default: return f32 ? DiaVec<__nv_bfloat16, float>::RPT : DiaVec<__nv_bfloat16, double>::RPT;
     }
 }
 
 static int64_t csr_grid_for(const mspv_matrix* A);
 
-int64_t spmv_partials_needed(const mspv_matrix* A) {
+// CTAs of the fused-dot SpMV launch in FP64 or FP32 arithmetic: the number of p.q partials
+// it writes, which the CG's alpha kernel sums. Only DIA launches differ between the two
+// (BF16 values: 8 rows per thread in FP64, 4 in FP32).
+int64_t spmv_partials_count(const mspv_matrix* A, bool f32) {
     switch (A->format) {
         case MSPV_DIA: {
-            const int64_t strip = (int64_t)kThreads * dia_rpt(A->value_type);
+            const int64_t strip = (int64_t)kThreads * dia_rpt(A->value_type, f32);
             const int64_t g = ((int64_t)A->nrows + strip - 1) / strip;
             return g < 1 ? 1 : g;
         }
@@ -1143,6 +1145,10 @@ int64_t spmv_partials_needed(const mspv_matrix* A) {
         default:
             return vector_grid(A->nrows);
     }
+}
+
+int64_t spmv_partials_needed(const mspv_matrix* A) {
+    return std::max(spmv_partials_count(A, false), spmv_partials_count(A, true));
 }
 
 template <typename VT, typename T>

@@ -173,6 +173,106 @@ def test_iterative_refinement(mspv, orc, vt, fmt, inner_fp32):
     assert np.max(np.abs(x - xo)) <= 1e-8
 
 
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_fp64_cg_on_low_precision_values_matches_oracle(mspv, orc, vt, fmt):
+    """FP64 CG on FP32 / BF16 stored values (the restarted refinement's FP64 inner solver):
+    same iteration count and iterate as the oracle's CG on the rounded matrix. The BF16 DIA
+    kernel runs 8 rows per thread in FP64 and 4 in FP32, so its p.q partial count differs
+    from the FP32 launch's: summing the wrong count corrupts alpha."""
+    g = 24
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 5)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    L = A.convert(fmt, vt)
+    Olo = orc.with_values(orc.convert(orc.canonicalize(n, n, r, c, v), fmt), vt)
+    b = synth.uniform_x(n, 8) - 0.5
+    res = L.cg(dev(b), tol=1e-10, maxit=1000)
+    xo, st, k, rel, _, _ = orc.cg(Olo, b, tol=1e-10, maxit=1000)
+    assert res.converged and st == orc.OK
+    assert abs(res.iters - k) <= 1
+    assert np.max(np.abs(res.x.cpu().numpy() - xo)) <= 1e-8 * np.max(np.abs(xo))
+    # and 25 fixed iterations track the oracle's iterate
+    res = L.cg(dev(b), tol=0.0, maxit=25)
+    xo, _, _, _, _, _ = orc.cg(Olo, b, tol=0.0, maxit=25)
+    assert np.max(np.abs(res.x.cpu().numpy() - xo)) <= 1e-10 * np.max(np.abs(xo))
+
+
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+@pytest.mark.parametrize("fmt", ["coo", "csr", "dia"])
+def test_reliable_updates_match_oracle(mspv, orc, vt, fmt):
+    """One FP32 CG with reliable FP64 residual updates on the perturbed stencil: reaches
+    1e-10 in the FP64 residual, agrees with the oracle's reliable-update CG (FP64
+    arithmetic) to the accuracy the tolerance fixes, and with FP32 values takes FP64 CG's
+    iteration count up to FP32 rounding."""
+    g = 20
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 3)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    A64 = A.convert(fmt)
+    Alo = A.convert(fmt, vt)
+    O = orc.convert(orc.canonicalize(n, n, r, c, v), fmt)
+    Olo = orc.with_values(O, vt)
+    b = orc.spmv(O, synth.uniform_x(n, 6) + 0.5)
+    delta = 1e-2 if vt == "f32" else 1e-1
+    res = A64.cg_ru(Alo, dev(b), tol=1e-10)          # library default delta for the value type
+    xo, st, nu, it, rel = orc.cg_ru(O, Olo, b, tol=1e-10, delta=delta)
+    assert res.converged and st == orc.OK
+    assert res.relres <= 1e-10
+    x = res.x.cpu().numpy()
+    assert np.linalg.norm(b - orc.spmv(O, x)) / np.linalg.norm(b) <= 1.5e-10
+    assert np.max(np.abs(x - xo)) <= 1e-8 * np.max(np.abs(xo))
+    _, _, k64, _, _, _ = orc.cg(O, b, tol=1e-10, maxit=2000)
+    if vt == "f32":
+        assert abs(res.iters - k64) <= 3 and abs(res.iters - it) <= 3
+    else:
+        assert res.iters <= 1.5 * it
+    assert 1 <= res.outer_iters <= nu + 3
+
+
+def test_reliable_updates_large_dia(mspv):
+    """64^3 perturbed stencil (262,144 rows) in DIA: FP32 values take at most 5% more
+    iterations than FP64 CG, BF16 values at most 40% more; both reach 1e-10."""
+    g = 64
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 3)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    D = A.convert("dia")
+    b = D.spmv(dev(synth.uniform_x(n, 7) + 0.5))
+    ref = D.cg(b, tol=1e-10, maxit=5000)
+    assert ref.converged
+    for vt, factor in (("f32", 1.05), ("bf16", 1.4)):
+        res = D.cg_ru(A.convert("dia", vt), b, tol=1e-10, maxit=5000)
+        assert res.converged and res.relres <= 1e-10
+        assert res.iters <= factor * ref.iters + 2, (vt, res.iters, ref.iters)
+        true = torch.linalg.norm(b - D.spmv(res.x)) / torch.linalg.norm(b)
+        assert float(true) <= 1.5e-10
+
+
+def test_reliable_updates_special_cases(mspv, stencil16):
+    g, n, A, O = stencil16
+    D = A.convert("csr")
+    L = A.convert("csr", "f32")
+    # b = 0: x = 0 without iterating
+    res = D.cg_ru(L, torch.zeros(n, dtype=torch.float64, device="cuda"),
+                  x=torch.ones(n, dtype=torch.float64, device="cuda"))
+    assert res.converged and res.iters == 0 and res.outer_iters == 0 and not torch.any(res.x)
+    # start at the solution (the stencil maps ones to its row sums)
+    b = D.spmv(torch.ones(n, dtype=torch.float64, device="cuda"))
+    res = D.cg_ru(L, b, x=torch.ones(n, dtype=torch.float64, device="cuda"))
+    assert res.converged and res.iters == 0 and res.outer_iters == 0
+    # iteration limit: not converged after exactly maxit FP32 iterations
+    res = D.cg_ru(L, b, tol=1e-14, maxit=7)
+    assert res.status == 6 and res.iters == 7 and res.outer_iters >= 1
+    # update limit
+    res = D.cg_ru(L, b, tol=1e-14, delta=0.9, max_updates=2)
+    assert res.status == 6 and res.outer_iters == 2
+    with pytest.raises(mspv.MspvError, match="EINVAL"):
+        D.cg_ir(L, b, inner_fp32=3)
+    with pytest.raises(mspv.MspvError, match="EFORMAT"):
+        D.cg_ru(D, b)
+
+
 def test_fp32_inner_needs_low_precision_values(mspv, stencil16):
     g, n, A, O = stencil16
     D = A.convert("dia")

@@ -361,6 +361,85 @@ def test_cg_ir_reaches_fp64_tolerance_with_bf16_values(orc):
     assert true <= 1e-10 and np.max(np.abs(x - 1)) < 1e-8
 
 
+def test_cg_ru_iterates_match_exact_rational_cg(orc):
+    """With both matrices equal, the replaced residual is the recursive one up to rounding,
+    so reliable updates after every iteration (delta = 2) reproduce the textbook iterates
+    of exact rational CG: this pins the direction p = r + beta p formed after each update."""
+    rng = np.random.default_rng(12)
+    n = 7
+    B = rng.integers(-3, 4, size=(n, n))
+    M = B @ B.T + n * np.eye(n, dtype=np.int64)
+    b = rng.integers(-5, 6, size=n)
+    exact = _exact_cg([[Fraction(int(t)) for t in row] for row in M],
+                      [Fraction(int(t)) for t in b], n - 1)
+    rows, cols = np.nonzero(M)
+    A = orc.canonicalize(n, n, rows, cols, M[rows, cols].astype(float))
+    for k in range(1, n):
+        for delta in (2.0, 1e-30):   # update after every iteration / only at maxit
+            x, st, nu, it, _ = orc.cg_ru(A, A, b.astype(float), tol=1e-300, delta=delta, maxit=k)
+            assert it == k and nu == (k if delta > 1 else 1)
+            assert np.allclose(x, exact[k - 1], rtol=1e-12, atol=1e-12)
+
+
+def test_cg_ru_finite_termination(orc):
+    """SPD diagonal with m distinct eigenvalues: at most m iterations, as for CG."""
+    for m in (1, 2, 3, 5):
+        n = 120
+        eig = np.linspace(1.0, 10.0, m)
+        d = eig[np.arange(n) % m]
+        A = orc.canonicalize(n, n, np.arange(n), np.arange(n), d)
+        b = synth.uniform_x(n, m) + 0.5
+        x, st, nu, it, rel = orc.cg_ru(A, A, b, tol=1e-12, delta=1e-2, maxit=50)
+        assert st == orc.OK and it <= m and rel <= 1e-12
+        assert np.allclose(x, b / d, rtol=1e-11)
+
+
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+def test_cg_ru_solves_the_fp64_system(orc, vt):
+    """Perturbed SPD stencil whose values round in FP32 / BF16: the answer is the solution
+    of the FP64 system by dense elimination (not that of the rounded matrix), with the
+    error bound cond(A) * tol; equal matrices take exactly textbook CG's iteration count."""
+    g = 6
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 3)
+    A = orc.canonicalize(n, n, r, c, v)
+    Alo = orc.with_values(A, vt)
+    assert not np.array_equal(Alo.av, A.av)
+    D = dense_of(n, n, A.ai, A.aj, A.av)
+    Dlo = dense_of(n, n, Alo.ai, Alo.aj, Alo.av)
+    b = synth.uniform_x(n, 2) - 0.5
+    xs = np.linalg.solve(D, b)
+    x_lo = np.linalg.solve(Dlo, b)
+    cond = np.linalg.cond(D)
+    tol = 1e-11
+    x, st, nu, it, rel = orc.cg_ru(A, Alo, b, tol=tol, delta=0.1, maxit=2000)
+    assert st == orc.OK and rel <= tol and nu >= 2
+    assert np.linalg.norm(b - D @ x) / np.linalg.norm(b) <= tol * 1.01
+    err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    assert err <= 2 * cond * tol
+    # the rounded matrix's own solution is far off: the pin sees which system was solved
+    assert np.linalg.norm(x_lo - xs) / np.linalg.norm(xs) > 1e3 * err
+    xc, stc, kc, _, _, _ = orc.cg(A, b, tol=tol, maxit=2000)
+    x2, st2, nu2, it2, _ = orc.cg_ru(A, A, b, tol=tol, delta=0.1, maxit=2000)
+    assert st2 == orc.OK and abs(it2 - kc) <= 1
+
+
+def test_cg_ru_special_cases(orc):
+    n = 10
+    A = orc.canonicalize(n, n, np.arange(n), np.arange(n), np.arange(1.0, n + 1))
+    x, st, nu, it, rel = orc.cg_ru(A, A, np.zeros(n), x0=np.ones(n))
+    assert st == orc.OK and nu == 0 and it == 0 and np.all(x == 0)
+    x, st, nu, it, rel = orc.cg_ru(A, A, np.arange(1.0, n + 1), x0=np.ones(n))
+    assert st == orc.OK and nu == 0 and it == 0
+    x, st, nu, it, rel = orc.cg_ru(A, A, np.ones(n), tol=1e-14, maxit=3)
+    assert st == orc.NOTCONV and it == 3 and nu >= 1 and rel > 1e-14
+    x, st, nu, it, rel = orc.cg_ru(A, A, np.ones(n), tol=1e-14, delta=0.999, max_updates=2)
+    assert st == orc.NOTCONV and nu == 2
+    Aind = orc.canonicalize(2, 2, np.array([0, 1]), np.array([0, 1]), np.array([1.0, -1.0]))
+    x, st, nu, it, rel = orc.cg_ru(Aind, Aind, np.array([1.0, 1.0]))
+    assert st == orc.BREAKDOWN and it == 0 and np.all(x == 0)
+
+
 @pytest.mark.parametrize("dims", [(3, 4, 5), (6, 6, 6), (9, 5, 7)])
 def test_hpcg_rank_split_closed_forms(orc, dims):
     """An interior process's matrix: 27 entries per row; the local part is the block's own
