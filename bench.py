@@ -603,6 +603,17 @@ def run_mixed(args, world, rank, local):
     os.environ["MSPV_CG_CHECK_EVERY"] = "10"
     ones = torch.ones(n, dtype=torch.float64, device=dev)
 
+    only = {e.strip() for e in args.mixed_only.split(",") if e.strip()}
+
+    class Results(dict):   # drops the solvers --mixed-only leaves out
+        def __init__(self, fmt):
+            super().__init__()
+            self.fmt = fmt
+
+        def run(self, label, fn):
+            if not only or f"{self.fmt}:{label}" in only:
+                self[label] = timed(fn)
+
     def timed(fn):
         xx = torch.zeros(n, dtype=torch.float64, device=dev)
         fn(xx)
@@ -624,35 +635,38 @@ def run_mixed(args, world, rank, local):
     clocks.start()
     results = {}
     for fmt in ("csr", "dia"):
+        if only and not any(e.startswith(fmt + ":") for e in only):
+            continue
         M = A.convert(fmt)
         b = M.spmv(ones)
-        out = {"fp64_cg": timed(lambda xx: M.cg(b, x=xx, tol=1e-10, maxit=20000))}
+        out = Results(fmt)
+        out.run("fp64_cg", lambda xx: M.cg(b, x=xx, tol=1e-10, maxit=20000))
         for vt in ("f32", "bf16"):
             L = A.convert(fmt, vt)
-            out[f"ir_{vt}_values_fp64_inner"] = timed(
-                lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=1e-5, max_outer=30, maxit_inner=20000))
-            out[f"ir_{vt}_values_fp32_inner"] = timed(
-                lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=args.ir_inner_tol, max_outer=30,
-                                   maxit_inner=20000, inner_fp32=True))
-            out[f"ru_{vt}_values"] = timed(lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, maxit=20000))
+            out.run(f"ir_{vt}_values_fp64_inner",
+                    lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=1e-5, max_outer=30, maxit_inner=20000))
+            out.run(f"ir_{vt}_values_fp32_inner",
+                    lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=args.ir_inner_tol, max_outer=30,
+                                       maxit_inner=20000, inner_fp32=True))
+            out.run(f"ru_{vt}_values", lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, maxit=20000))
             L.close()
         if fmt == "dia":   # inner tolerance of the restarted solver, update threshold of the reliable one
             L = A.convert(fmt, "bf16")
             for itol in (1e-3, 1e-4, 1e-5, 1e-7):
-                out[f"ir_bf16_values_fp32_inner_tol{itol:g}"] = timed(
-                    lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=itol, max_outer=40, maxit_inner=20000,
-                                       inner_fp32=True))
+                out.run(f"ir_bf16_values_fp32_inner_tol{itol:g}",
+                        lambda xx: M.cg_ir(L, b, x=xx, tol=1e-10, inner_tol=itol, max_outer=40,
+                                           maxit_inner=20000, inner_fp32=True))
             for d in (0.03, 0.3):
-                out[f"ru_bf16_values_delta{d:g}"] = timed(
-                    lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, delta=d, max_updates=200, maxit=20000))
+                out.run(f"ru_bf16_values_delta{d:g}",
+                        lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, delta=d, max_updates=200, maxit=20000))
             L.close()
             L = A.convert(fmt, "f32")
             for d in (1e-3, 1e-1):
-                out[f"ru_f32_values_delta{d:g}"] = timed(
-                    lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, delta=d, max_updates=200, maxit=20000))
+                out.run(f"ru_f32_values_delta{d:g}",
+                        lambda xx: M.cg_ru(L, b, x=xx, tol=1e-10, delta=d, max_updates=200, maxit=20000))
             L.close()
         M.close()
-        results[fmt] = out
+        results[fmt] = dict(out)
     clk = clocks.stop()
     best = min((v["ms"], f, k) for f, o in results.items() for k, v in o.items() if v["converged"])
     out = {"metric": MIXED_METRIC, "value": best[0], "unit": "ms", "higher_is_better": False,
@@ -846,6 +860,9 @@ def main():
                          "CG vs FP32/BF16-value refinement on a large stencil; split: one HPCG "
                          "process's matrix, whole vs local/remote formats")
     ap.add_argument("--mixed-grid", type=int, default=192, help="mixed mode: stencil grid")
+    ap.add_argument("--mixed-only", default="",
+                    help="mixed mode: comma-separated format:solver entries to run (default all), "
+                         "e.g. dia:ru_bf16_values")
     ap.add_argument("--matrices", type=int, default=2000, help="selector mode: synthetic matrices")
     ap.add_argument("--tune-reps", type=int, default=10, help="selector mode: timed SpMV per format")
     ap.add_argument("--epochs", type=int, default=300, help="selector mode: training epochs")
