@@ -1,8 +1,10 @@
-"""Full-size parity on the benchmark workload: the 27-point stencil on a 128^3 grid
+"""Full-size parity on the benchmark workloads: the 27-point stencil on a 128^3 grid
 (n = 2,097,152, nnz = 382^3 = 55,742,968) in COO, CSR and DIA, in the launch
 configuration the benchmark times, against the oracle on the whole output; plus the
 separable closed form A x = 27 x - (T (x) T (x) T) x as a size-independent property,
-and 50 FP64 CG iterations against the oracle's."""
+and 50 FP64 CG iterations against the oracle's. At 192^3 (the mixed-precision workload)
+and 256^3 (the format-selection workload), where the oracle would take minutes, the
+closed form checks every SpMV output and the FP64 residual of each solver's answer."""
 import numpy as np
 import pytest
 
@@ -39,8 +41,9 @@ def big(mspv, orc):
     return n, mats
 
 
-def sep_apply(x):
-    x3 = x.reshape(G, G, G)
+def sep_apply(x, g=G):
+    """(A x, sum_j |a_ij x_j|) of the g^3 stencil by three separable 3-point passes."""
+    x3 = x.reshape(g, g, g)
     out = x3
     for ax in range(3):
         s = out.copy()
@@ -81,3 +84,62 @@ def test_fullsize_cg_50_iterations(mspv, orc, big):
         M, _ = mats[fmt]
         r2 = M.cg(torch.from_numpy(b).cuda(), tol=0.0, maxit=50)
         assert np.max(np.abs(r2.x.cpu().numpy() - xo)) <= 1e-10 * np.max(np.abs(xo))
+
+
+def stencil_on_device(mspv, g):
+    n = g ** 3
+    r, c, v = synth.stencil27_torch(g, "cuda")
+    A = mspv.Matrix.from_coo(n, n, r, c, v)
+    del r, c, v
+    return n, A
+
+
+def test_192_mixed_precision_solvers_reach_fp64_residual(mspv):
+    """192^3 (n = 7,077,888, nnz = 574^3): FP64 CG, restarted FP32-inner refinement and
+    reliable updates with FP32 / BF16 DIA values, each to 1e-10, checked by the FP64
+    residual of the closed form; FP64 CG's count also against the CG bound from the
+    stencil's condition number (sqrt(kappa)/2 ln(2/tol), kappa ~ 5,032)."""
+    g = 192
+    n, A = stencil_on_device(mspv, g)
+    assert A.info["nnz"] == (3 * g - 2) ** 3
+    D = A.convert("dia")
+    b_host, _ = sep_apply(np.ones(n), g)
+    b = torch.from_numpy(b_host).cuda()
+    bn = np.linalg.norm(b_host)
+
+    def check(res, limit):
+        assert res.converged
+        x = res.x.cpu().numpy()
+        ax, _ = sep_apply(x, g)
+        assert np.linalg.norm(b_host - ax) / bn <= 1.2e-10
+        assert np.linalg.norm(x - 1.0) / np.sqrt(n) <= 5032 * 1.2e-10   # kappa * relres
+        assert res.iters <= limit
+
+    ref = D.cg(b, tol=1e-10, maxit=5000)
+    check(ref, int(np.sqrt(5032) / 2 * np.log(2 / 1e-10)) + 1)
+    for vt in ("f32", "bf16"):
+        L = A.convert("dia", vt)
+        check(D.cg_ru(L, b, tol=1e-10, maxit=5000), int(1.4 * ref.iters))
+        check(D.cg_ir(L, b, tol=1e-10, inner_tol=1e-6, max_outer=30, maxit_inner=5000, inner_fp32=1),
+              int(2.0 * ref.iters))
+        L.close()
+    D.close()
+    A.close()
+
+
+def test_256_spmv_closed_form(mspv):
+    """256^3 (n = 16,777,216, nnz = 766^3 = 449,455,096): every output row of the SpMV in
+    each format at the format-selection workload's size against the separable closed form."""
+    g = 256
+    n, A = stencil_on_device(mspv, g)
+    assert A.info["nnz"] == (3 * g - 2) ** 3
+    x = synth.uniform_x(n, 3)
+    want, scale = sep_apply(x, g)
+    xd = torch.from_numpy(x).cuda()
+    for fmt in ("coo", "csr", "dia"):
+        M = A if fmt == "coo" else A.convert(fmt)
+        y = M.spmv(xd).cpu().numpy()
+        assert np.all(np.abs(y - want) <= 1e-13 * scale), fmt
+        if M is not A:
+            M.close()
+    A.close()
