@@ -332,6 +332,15 @@ MSPV_API const char* mspv_status_string(mspv_status s);
  */
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max);
 
+/*
+ * Device-side wait status (host call, synchronous with the device). The DIA SpMV that streams
+ * its operands with bulk asynchronous copies bounds every wait on a copy; a wait that runs out
+ * (not expected on a healthy device) leaves that SpMV's y incomplete and is recorded on the
+ * device. Returns ECUDA once that has happened in this process (with a message), else OK.
+ * The CG solvers check it before they return.
+ */
+MSPV_API mspv_status mspv_device_status(void);
+
 /* Library version, as MAJOR * 10000 + MINOR * 100 + PATCH. */
 MSPV_API int32_t mspv_version(void);
 

@@ -115,6 +115,12 @@ MSPV_API const char* mspv_status_string(mspv_status s) {
 
 MSPV_API int32_t mspv_version(void) { return 100; }
 
+MSPV_API mspv_status mspv_device_status(void) {
+    MSPV_GUARD_BEGIN
+    return check_device_fault();
+    MSPV_GUARD_END
+}
+
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max) {
     return choose_csr_vector(row_mean, row_std, row_max);
 }
