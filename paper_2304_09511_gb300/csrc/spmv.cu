@@ -13,7 +13,9 @@
 //      value load per diagonal) and walks the diagonals in order with the predicate
 //      0 <= k < N -- the row-parallel, diagonal-sequential structure of the paper's
 //      outer-loop SVE vectorisation (Sec. III), with warp lanes in place of SVE lanes.
-//      The FP32-arithmetic kernel reads one x window per run of consecutive offsets.
+//      The FP32-arithmetic kernel reads one x window per run of consecutive offsets, at
+//      4 rows per thread for FP32 values and 8 (one 16-byte value load per diagonal,
+//      128-thread CTAs) for BF16 values.
 //      A bulk-copy variant (opt-in, MSPV_DIA_BULK=1; measured slower, see dia_bulk_enabled):
 //      one persistent CTA per SM, each strip's diagonal slices and per-run x slices brought
 //      into a multi-stage shared-memory ring by bulk asynchronous copies (TMA engine,
@@ -88,13 +90,15 @@ template <> struct DiaVec<float, float> {
     }
 };
 template <> struct DiaVec<__nv_bfloat16, float> {
-    static constexpr int RPT = 4;   // an 8-byte value load per diagonal, as many rows as FP32
+    static constexpr int RPT = 8;   // a 16-byte value load per diagonal (half the requests of 4 rows)
     __device__ __forceinline__ static void load(const __nv_bfloat16* p, float (&v)[RPT]) {
-        const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
-        v[0] = __uint_as_float(t.x << 16);
-        v[1] = __uint_as_float(t.x & 0xffff0000u);
-        v[2] = __uint_as_float(t.y << 16);
-        v[3] = __uint_as_float(t.y & 0xffff0000u);
+        const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
     }
 };
 
@@ -217,27 +221,39 @@ __device__ __forceinline__ void dia_f32_fma(const float (&a)[RPT], const float (
     for (int r = 0; r < RPT; ++r) acc[r] = fmaf(a[r], w[M + r], acc[r]);
 }
 
+// CTA size of the FP32-arithmetic DIA kernel: 128 threads at 8 rows per thread (BF16 values,
+// 55 registers), 256 at 4 (FP32 values); a CTA covers 1,024 rows either way.
+template <typename VT> struct DiaF32Shape { static constexpr int NT = kThreads; };
+template <> struct DiaF32Shape<__nv_bfloat16> { static constexpr int NT = 128; };
+
 template <typename VT>
-__global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
+__global__ void __launch_bounds__(DiaF32Shape<VT>::NT) spmv_dia_f32_kernel(
     int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff, const int2* __restrict__ runs,
     int32_t nruns, const VT* __restrict__ av, const float* __restrict__ x, float* __restrict__ y, DotEpilogue ep) {
-    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 or BF16 values)
-    static_assert(RPT == 4, "the run window is sized for 4 rows per thread");
-    constexpr int W = 12;                          // shift m + t <= 5, plus 4 rows, in 3 float4
+    constexpr int RPT = DiaVec<VT, float>::RPT;   // 4 (FP32 values) or 8 (BF16 values)
+    constexpr int NT = DiaF32Shape<VT>::NT;
+    static_assert(RPT == 4 || RPT == 8, "x windows come in whole float4s");
+    constexpr int W = RPT + 8;                     // shift m + t <= 5 plus RPT rows, in float4s
     pdl_wait();
     pdl_trigger();
     if (ep.st && ep.st->done) return;
+    // At 8 rows per thread the run table sits in shared memory, so that no global load heads
+    // each run (192^3 BF16: 75.7 vs 86.3 us); at 4 rows the global read measured faster.
+    constexpr bool kRunsInSmem = RPT == 8;
     __shared__ int32_t s_off[kDiaSmemDiags];
-    for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += kThreads) s_off[k] = doff[k];
+    __shared__ int2 s_runs[kRunsInSmem ? kDiaSmemDiags : 1];
+    for (int k = threadIdx.x; k < ndiags && k < kDiaSmemDiags; k += NT) s_off[k] = doff[k];
+    if constexpr (kRunsInSmem)
+        for (int k = threadIdx.x; k < nruns && k < kDiaSmemDiags; k += NT) s_runs[k] = runs[k];
     __syncthreads();
-    const int64_t i0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * RPT;
+    const int64_t i0 = ((int64_t)blockIdx.x * NT + threadIdx.x) * RPT;
     float acc[RPT];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) acc[r] = 0.0f;
     if (i0 < n) {
         const VT* col = av + i0;
         for (int q = 0; q < nruns; ++q) {
-            const int2 run = __ldg(runs + q);
+            const int2 run = (kRunsInSmem && q < kDiaSmemDiags) ? s_runs[q] : __ldg(runs + q);
             const int j0 = run.x, len = run.y;
             float a[3][RPT];
 #pragma unroll
@@ -289,13 +305,17 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
     }
     float d = 0.0f;
     if (!ep.acc && i0 + RPT <= n) {   // the vector store overwrites; accumulation goes below
-        reinterpret_cast<float4*>(y + i0)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        if (ep.st) {
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(x + i0));
-            d = fmaf(xv.x, acc[0], d);
-            d = fmaf(xv.y, acc[1], d);
-            d = fmaf(xv.z, acc[2], d);
-            d = fmaf(xv.w, acc[3], d);
+#pragma unroll
+        for (int u = 0; u < RPT / 4; ++u) {
+            reinterpret_cast<float4*>(y + i0)[u] =
+                make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+            if (ep.st) {
+                const float4 xv = __ldg(reinterpret_cast<const float4*>(x + i0) + u);
+                d = fmaf(xv.x, acc[4 * u], d);
+                d = fmaf(xv.y, acc[4 * u + 1], d);
+                d = fmaf(xv.z, acc[4 * u + 2], d);
+                d = fmaf(xv.w, acc[4 * u + 3], d);
+            }
         }
     } else if (i0 < n) {
 #pragma unroll
@@ -305,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dia_f32_kernel(
                 if (ep.st) d = fmaf(__ldg(x + i0 + r), acc[r], d);
             }
     }
-    if (ep.st) finish_dot(d, ep);
+    if (ep.st) finish_dot_nt<float, NT>(d, ep);
 }
 
 // ---------------------------------------------------------------------------
@@ -1406,12 +1426,17 @@ static void allow_smem(size_t bytes) {
 // CTAs run on consecutive strips, so the CTAs in flight read one contiguous stretch of
 // each diagonal and of x (DRAM and L2 friendly). Spreading one wave of CTAs over distant
 // equal row ranges instead balances the tail but measured ~10% slower on GB300.
-// Rows per thread of the DIA kernel that a value type and arithmetic launch.
-static int64_t dia_rpt(int vt, bool f32) {
+// Rows per CTA of the DIA kernel that a value type and arithmetic launch (threads x rows per
+// thread).
+static int64_t dia_strip_rows(int vt, bool f32) {
     switch (vt) {
-        case MSPV_F64: return DiaVec<double, double>::RPT;
-        case MSPV_F32: return f32 ? DiaVec<float, float>::RPT : DiaVec<float, double>::RPT;
-        default: return f32 ? DiaVec<__nv_bfloat16, float>::RPT : DiaVec<__nv_bfloat16, double>::RPT;
+        case MSPV_F64: return (int64_t)kThreads * DiaVec<double, double>::RPT;
+        case MSPV_F32:
+            return f32 ? (int64_t)DiaF32Shape<float>::NT * DiaVec<float, float>::RPT
+                       : (int64_t)kThreads * DiaVec<float, double>::RPT;
+        default:
+            return f32 ? (int64_t)DiaF32Shape<__nv_bfloat16>::NT * DiaVec<__nv_bfloat16, float>::RPT
+                       : (int64_t)kThreads * DiaVec<__nv_bfloat16, double>::RPT;
     }
 }
 
@@ -1487,7 +1512,7 @@ int64_t spmv_partials_count(const mspv_matrix* A, bool f32) {
         case MSPV_DIA: {
             const DiaBulkPlan bp = dia_bulk_plan_for(A, f32);
             if (bp.use) return bp.grid;
-            const int64_t strip = (int64_t)kThreads * dia_rpt(A->value_type, f32);
+            const int64_t strip = dia_strip_rows(A->value_type, f32);
             const int64_t g = ((int64_t)A->nrows + strip - 1) / strip;
             return g < 1 ? 1 : g;
         }
@@ -1526,11 +1551,12 @@ static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         }
     }
     constexpr int RPT = DiaVec<VT, T>::RPT;
-    const int64_t strip = (int64_t)kThreads * RPT;
+    constexpr int NT = sizeof(T) == 4 ? DiaF32Shape<VT>::NT : kThreads;
+    const int64_t strip = (int64_t)NT * RPT;
     int64_t grid = ((int64_t)A->nrows + strip - 1) / strip;
     if (grid < 1) grid = 1;
     if constexpr (sizeof(T) == 4) {
-        launch_kernel(ep.pdl, spmv_dia_f32_kernel<VT>, (unsigned)grid, kThreads, 0, s, A->nrows, A->ndiags,
+        launch_kernel(ep.pdl, spmv_dia_f32_kernel<VT>, (unsigned)grid, NT, 0, s, A->nrows, A->ndiags,
                       A->npad, A->doff, (const int2*)A->druns, A->ndruns, static_cast<const VT*>(A->av), x, y, ep);
     } else {
         if (ep.acc)
