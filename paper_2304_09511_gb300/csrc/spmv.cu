@@ -222,7 +222,7 @@ __device__ __forceinline__ void dia_f32_fma(const float (&a)[RPT], const float (
 }
 
 // CTA size of the FP32-arithmetic DIA kernel: 128 threads at 8 rows per thread (BF16 values,
-// 55 registers), 256 at 4 (FP32 values); a CTA covers 1,024 rows either way.
+// 56 registers), 256 at 4 (FP32 values); a CTA covers 1,024 rows either way.
 template <typename VT> struct DiaF32Shape { static constexpr int NT = kThreads; };
 template <> struct DiaF32Shape<__nv_bfloat16> { static constexpr int NT = 128; };
 
