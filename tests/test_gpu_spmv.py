@@ -123,6 +123,32 @@ def test_banded_structure_and_spmv(mspv, orc, case, fmt):
     assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), O, x, orc)
 
 
+@pytest.mark.parametrize("arith", ["f64", "f32", "bf16"])
+def test_dia_more_diagonals_than_shared_tables(mspv, orc, arith):
+    """600 scattered diagonals (about 550 runs of consecutive offsets): past the 256 offsets and
+    runs the DIA kernels cache in shared memory they read the tables from global memory; FP64
+    SpMV and FP32-arithmetic SpMV (FP32 / BF16 values) against the oracle."""
+    n, k = 4003, 600
+    r, c, v = synth.banded(n, k, 17, 0.8, 1900)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    vt = "f64" if arith == "f64" else arith
+    D = A.convert("dia", vt)
+    O = orc.with_values(orc.coo_to_dia(orc.canonicalize(n, n, r, c, v)), vt)
+    assert O.ndiags == k and D.info["ndiags"] == k
+    if arith == "f64":
+        x = synth.uniform_x(n, 18) * 2 - 1
+        assert_spmv_parity(D.spmv(dev(x)).cpu().numpy(), O, x, orc)
+        return
+    x32 = (synth.uniform_x(n, 18) * 2 - 1).astype(np.float32)
+    y = D.spmv_f32(dev(x32)).cpu().numpy().astype(np.float64)
+    x64 = x32.astype(np.float64)
+    want = orc.spmv(O, x64)
+    absO = orc.Matrix(O.fmt, O.nrows, O.ncols, O.nnz, ai=O.ai, aj=O.aj, irp=O.irp, av=np.abs(O.av),
+                      doff=O.doff, npad=O.npad)
+    bound = 2.0 * (k + 2) * 2.0 ** -24 * orc.spmv(absO, np.abs(x64)) + 1e-30
+    assert np.all(np.abs(y - want) <= bound)
+
+
 @pytest.mark.parametrize("vec", ["0w", "0b", 1, 2, 4, 8, 16, 32])
 def test_csr_every_kernel_choice(mspv, orc, vec, monkeypatch):
     if isinstance(vec, str):   # staged kernels: warp-private slices or CTA row blocks
