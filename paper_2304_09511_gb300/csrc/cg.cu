@@ -455,6 +455,14 @@ static int check_every() {
     return v > 0 ? v : 10;
 }
 
+// Iterations launched between two polls of the stop flag: MSPV_CG_CHECK_EVERY when set, else
+// 10; a run with tol <= 0 has a fixed count (only a breakdown stops it early, and launches past
+// it are no-ops), so it is launched in one batch and the GPU is not drained to poll.
+static int32_t poll_batch(double tol, int32_t remaining) {
+    if (tol <= 0.0 && !std::getenv("MSPV_CG_CHECK_EVERY")) return remaining;
+    return std::min<int32_t>(check_every(), remaining);
+}
+
 // The CG iteration loop shared by the FP64 and the FP32-arithmetic solver: V is the
 // vector type, Spmv(x, y, ep) launches the SpMV with its p.q partials.
 template <typename V, typename SpmvFn, typename UpdateK, typename PupdateK>
@@ -467,13 +475,13 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
     const int64_t P = spmv_partials_count(A, sizeof(V) == sizeof(float));   // exactly the partials the SpMV writes
     const bool pdl = use_pdl();
     const DotEpilogue ep{w.st, w.partials, pdl};
-    const int every = check_every();
+    const double tol = hst->tol;
     int32_t launched = 0;
     for (;;) {
         MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         MSPV_CUDA_TRY(cudaStreamSynchronize(s));
         if (hst->done || launched >= maxit) break;
-        const int32_t batch = std::min<int32_t>(every, maxit - launched);
+        const int32_t batch = poll_batch(tol, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
             MSPV_SCALAR_LAUNCH(pdl, cg_alpha_kernel, P, s, (const double*)w.partials, P, w.st);
