@@ -274,7 +274,10 @@ def run_mspv(args, world, rank, local):
     cg_ms_iter = ms["cg"] / args.cg_iters
 
     # gpu launches of this library inside the timed region
-    coo_launches = 1 + (1 if (nnz + 511) // 512 > 1 else 0)   # segment kernel + carry fix-up
+    # COO: the row-block kernel alone (rows of at most 128 entries), else a chunked kernel + fix-up
+    coo_kernel = os.environ.get("MSPV_COO_KERNEL") or ("rb" if A.info["row_max"] <= 128 else "seg")
+    chunk = 512 if coo_kernel == "seg" else 256
+    coo_launches = 1 if coo_kernel == "rb" else 1 + (1 if (nnz + chunk - 1) // chunk > 1 else 0)
     # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update
     launches_per_step = coo_launches + 1 + 1 + (3 + 5 * args.cg_iters)
 

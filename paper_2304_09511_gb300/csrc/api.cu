@@ -174,7 +174,7 @@ MSPV_API mspv_status mspv_create_coo(int32_t nrows, int32_t ncols, int64_t nnz, 
     }
     if (st == MSPV_OK) st = build_coo(nrows, ncols, nnz, r, c, v, s, M);
     if (st == MSPV_OK) st = finish_coo_stats(M, s);
-    if (st == MSPV_OK) st = ensure_coo_carry(M);
+    if (st == MSPV_OK) st = ensure_coo_carry(M, s);
     if (st != MSPV_OK) {
         cudaStreamSynchronize(s);
         mspv_destroy(M);

@@ -548,7 +548,7 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
             M->bytes += nnz * 4;
             if (nnz > 0)
                 MSPV_CUDA_TRY(cudaMemcpyAsync(M->ai, src_ai, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s));
-            MSPV_TRY(ensure_coo_carry(M));
+            MSPV_TRY(ensure_coo_carry(M, s));
         } else {
             // irp = exclusive scan of the row histogram; irp[nrows] = nnz
             MSPV_TRY(dev_alloc_n(&M->irp, (int64_t)M->nrows + 1));
@@ -726,25 +726,44 @@ mspv_status split_columns(const mspv_matrix* A, int32_t c, cudaStream_t s, mspv_
         MSPV_CUDA_TRY(cudaGetLastError());
     }
     MSPV_TRY(finish_coo_stats(L, s));
-    MSPV_TRY(ensure_coo_carry(L));
+    MSPV_TRY(ensure_coo_carry(L, s));
     MSPV_TRY(finish_coo_stats(R, s));
-    MSPV_TRY(ensure_coo_carry(R));
+    MSPV_TRY(ensure_coo_carry(R, s));
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
     return MSPV_OK;
 }
 
-// COO kernel for the longest row: short rows (at most 128 entries) take the run-vector
-// kernel, whose 4 lanes per run gather neighbouring columns together (stencil-like rows);
+// COO kernel for the longest row: short rows (at most 128 entries) take the row-block
+// kernel (a warp per 8 consecutive rows, 4 lanes per row, chunks that never cut a row);
 // matrices with longer rows take the lane-sequential segment kernel, which keeps every lane
-// busy however the rows are cut. MSPV_COO_KERNEL=vec|seg overrides.
+// busy however the rows are cut. MSPV_COO_KERNEL=rb|vec|seg overrides (vec: the run-vector
+// kernel, fixed 256-entry chunks).
 int32_t choose_coo_kernel(int32_t row_max) {
     const char* k = std::getenv("MSPV_COO_KERNEL");
+    if (k && std::strcmp(k, "rb") == 0) return 2;
     if (k && std::strcmp(k, "vec") == 0) return 1;
     if (k && std::strcmp(k, "seg") == 0) return 0;
-    return row_max <= 128 ? 1 : 0;
+    return row_max <= 128 ? 2 : 0;
 }
 
-mspv_status ensure_coo_carry(mspv_matrix* M) {
+// First entry of every block of kCooRbRows rows in row-sorted COO (blocks past the last
+// entry start at nnz): the entry where the row index first reaches or passes a block's first
+// row records it, so every block boundary is written once.
+__global__ void coo_row_blocks_kernel(const int32_t* __restrict__ ai, int64_t nnz, int32_t* __restrict__ rb) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = ai[e];
+        const int32_t rp = e > 0 ? ai[e - 1] : -1;
+        if (r == rp) continue;
+        for (int64_t k = ((int64_t)rp + kCooRbRows) / kCooRbRows; k <= r / kCooRbRows; ++k) rb[k] = (int32_t)e;
+    }
+}
+
+__global__ void fill_i32_kernel(int32_t* __restrict__ v, int64_t n, int32_t value) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = value;
+}
+
+mspv_status ensure_coo_carry(mspv_matrix* M, cudaStream_t s) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
     M->coo_kernel = choose_coo_kernel(M->row_max);
     const char* ch = std::getenv("MSPV_COO_CHUNK");
@@ -752,6 +771,14 @@ mspv_status ensure_coo_carry(mspv_matrix* M) {
     M->nchunks = (M->nnz + kCooVecChunk - 1) / kCooVecChunk;
     MSPV_TRY(dev_alloc_n(&M->carry, M->nchunks > 0 ? M->nchunks : 1));
     M->bytes += (M->nchunks > 0 ? M->nchunks : 1) * (int64_t)sizeof(CooCarry);
+    if (M->coo_kernel == 2 && M->nrows > 0) {
+        M->coo_nrb = ((int64_t)M->nrows + kCooRbRows - 1) / kCooRbRows;
+        MSPV_TRY(dev_alloc_n(&M->coo_rb, M->coo_nrb + 1));
+        M->bytes += (M->coo_nrb + 1) * (int64_t)sizeof(int32_t);
+        fill_i32_kernel<<<grid_for(M->coo_nrb + 1), kThreads, 0, s>>>(M->coo_rb, M->coo_nrb + 1, (int32_t)M->nnz);
+        if (M->nnz > 0) coo_row_blocks_kernel<<<grid_for(M->nnz), kThreads, 0, s>>>(M->ai, M->nnz, M->coo_rb);
+        MSPV_CUDA_TRY(cudaGetLastError());
+    }
     return MSPV_OK;
 }
 
@@ -787,6 +814,9 @@ mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, do
 void free_matrix(mspv_matrix* M) {
     auto f = [](void* p) { if (p) dev_free(p, 0); };
     f(M->ai); f(M->aj); f(M->irp); f(M->doff); f(M->druns); f(M->av); f(M->carry); f(M->row_block); f(M->long_rows);
+    f(M->coo_rb);
+    M->coo_rb = nullptr;
+    M->coo_nrb = 0;
     f(M->cg.r); f(M->cg.p); f(M->cg.q); f(M->cg.partials); f(M->cg.st);
     f(M->cg.rf); f(M->cg.pf); f(M->cg.qf);
     if (M->cg.host_st) cudaFreeHost(M->cg.host_st);

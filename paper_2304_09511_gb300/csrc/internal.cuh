@@ -182,6 +182,7 @@ struct CooCarry {
 // staged in shared memory (16 B per entry, plus 4 B of row index for COO).
 constexpr int kCooWindow = 3072;    // staged COO kernel (allocation-free entry point)
 constexpr int kCooVecChunk = 256;   // run-vector COO kernel: entries per warp
+constexpr int kCooRbRows = 8;       // row-block COO kernel: rows per warp (4 lanes each)
 constexpr int kCsrWindow = 2560;     // a CTA takes the rows that start in its window
 
 // CG workspace, owned by a handle and grown on demand.
@@ -242,7 +243,9 @@ struct mspv_matrix {
 
     mspv::CooCarry* carry = nullptr;   // COO: per-window carries
     int64_t nchunks = 0;               // COO chunks of kCooVecChunk entries
-    int32_t coo_kernel = 0;            // COO: 0 lane-sequential segments, 1 run-vector (choose_coo_kernel)
+    int32_t coo_kernel = 0;            // COO: 0 lane-sequential segments, 1 run-vector, 2 row blocks (choose_coo_kernel)
+    int32_t* coo_rb = nullptr;         // COO row-block kernel: first entry of every 8-row block, nrb + 1 entries
+    int64_t coo_nrb = 0;
     int32_t coo_chunk = 256;           // run-vector kernel: entries per warp (256; MSPV_COO_CHUNK=512)
     int32_t* row_block = nullptr;      // CSR: first row of each window, nblocks + 1 entries
     int32_t* long_rows = nullptr;      // CSR vector kernel: rows longer than 32 * csr_vector
@@ -268,7 +271,7 @@ mspv_status export_matrix(const mspv_matrix* A, int32_t* idx0, int32_t* idx1, do
 void free_matrix(mspv_matrix* M);
 // DIA slots (ndiags * npad) allowed for nnz entries: max(MSPV_DIA_MAX_FILL (32) * nnz, 2^20)
 double dia_slot_cap(int64_t nnz);
-mspv_status ensure_coo_carry(mspv_matrix* M);
+mspv_status ensure_coo_carry(mspv_matrix* M, cudaStream_t s);   // stream-ordered after M->ai
 mspv_status finish_coo_stats(mspv_matrix* M, cudaStream_t s);
 // Local part (columns < c) and remote part (columns >= c, renumbered from 0) of a COO/CSR
 // handle, both canonical COO handles with A's value type.
@@ -291,7 +294,7 @@ int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
 mspv_status build_csr_long_rows(mspv_matrix* M, cudaStream_t s);
 int32_t choose_csr_block_kernel();   // MSPV_CSR_KERNEL=block selects CTA row blocks
-int32_t choose_coo_kernel(int32_t row_max);   // 1 run-vector, 0 lane-sequential segments
+int32_t choose_coo_kernel(int32_t row_max);   // 2 row blocks, 1 run-vector, 0 lane-sequential segments
 
 // cg.cu
 mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,

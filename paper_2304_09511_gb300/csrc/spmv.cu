@@ -1151,6 +1151,85 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
         for (int32_t z = rrow[nr - 1] + 1 + lane; z < nrows; z += 32) zero_y(y, z, acc);
 }
 
+// COO, a warp per block of kCooRbRows consecutive rows. The block's entries [rb[b], rb[b+1])
+// come from a table built with the handle (one int per 8 rows); a row never crosses a block,
+// so there are no carries and no fix-up pass. The warp reads the block's row indices 32 at a
+// time, marks where each row starts (ballot over row changes) in shared memory, then 4 lanes
+// per row (one row per lane group, the whole block in one pass) accumulate lane-strided FMAs
+// and join them with two shuffle-adds: the CSR V = 4 instruction count with every row index
+// still read. Rows of the block without entries are written as 0 (left as they are for
+// y += A x). For rows of at most 128 entries (longer ones take the segment kernel).
+template <typename VT, typename T>
+__global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
+    int32_t nrows, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj, const VT* __restrict__ av,
+    const int32_t* __restrict__ rb, int64_t nrb, const T* __restrict__ x, T* __restrict__ y, const CgState* st,
+    bool acc) {
+    static_assert(kCooRbRows * 4 == 32, "one warp: kCooRbRows rows of 4 lanes");
+    pdl_wait();
+    pdl_trigger();
+    if (st && st->done) return;
+    __shared__ int32_t s_start[kThreads / 32][kCooRbRows];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * (kThreads / 32) + w;
+    if (b >= nrb) return;   // whole warp
+    const int32_t row0 = (int32_t)(b * kCooRbRows);
+    const int64_t e0 = __ldg(rb + b);
+    const int cnt = (int)(__ldg(rb + b + 1) - e0);
+    int32_t* start = s_start[w];
+    if (lane < kCooRbRows) start[lane] = -1;
+    __syncwarp();
+    // The first 256 row indices are loaded together (8 independent loads per lane, the whole
+    // block of 8 stencil-like rows), the rest 32 at a time.
+    constexpr int kHeld = 8;
+    int32_t rv[kHeld];
+#pragma unroll
+    for (int q = 0; q < kHeld; ++q) {
+        const int k = q * 32 + lane;
+        rv[q] = (k < cnt) ? __ldcs(ai + e0 + k) : INT_MAX;
+    }
+    int32_t last = row0 - 1;   // row of the entry before the current 32
+#pragma unroll
+    for (int q = 0; q < kHeld; ++q) {
+        const int k = q * 32 + lane;
+        const int32_t r = rv[q];
+        int32_t prev = __shfl_up_sync(FULL, r, 1);
+        if (lane == 0) prev = last;
+        if (k < cnt && r != prev) start[r - row0] = k;
+        last = __shfl_sync(FULL, r, 31);
+    }
+    for (int k0 = kHeld * 32; k0 < cnt; k0 += 32) {
+        const int k = k0 + lane;
+        const int32_t r = (k < cnt) ? __ldcs(ai + e0 + k) : INT_MAX;
+        int32_t prev = __shfl_up_sync(FULL, r, 1);
+        if (lane == 0) prev = last;
+        if (k < cnt && r != prev) start[r - row0] = k;
+        last = __shfl_sync(FULL, r, 31);
+    }
+    __syncwarp();
+    const int grp = lane >> 2, sub = lane & 3;
+    const int32_t row = row0 + grp;
+    const int bg = start[grp];
+    int eg = cnt;   // the next row of the block that has entries starts where this one ends
+    for (int g2 = grp + 1; g2 < kCooRbRows; ++g2)
+        if (start[g2] >= 0) {
+            eg = start[g2];
+            break;
+        }
+    T sum = T(0);
+    if (bg >= 0) {
+#pragma unroll 4
+        for (int j = bg + sub; j < eg; j += 4)
+            sum = fma_t(convert_value<T>(__ldcs(av + e0 + j)), __ldg(x + __ldcs(aj + e0 + j)), sum);
+    }
+    sum += __shfl_xor_sync(FULL, sum, 1);
+    sum += __shfl_xor_sync(FULL, sum, 2);
+    if (sub == 0 && row < nrows) {
+        if (bg >= 0) store_y(y, row, sum, acc);
+        else zero_y(y, row, acc);
+    }
+}
+
 // Rows spanning windows: the window where such a row starts adds its tail, the heads of
 // the windows it covers entirely, and the head of the window where it ends, in order.
 template <typename T>
@@ -1682,7 +1761,13 @@ static void launch_coo_windows(int32_t nrows, int64_t nnz, const int32_t* ai, co
 template <typename VT, typename T>
 static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
     int64_t nch;
-    if (A->coo_kernel == 1) {
+    if (A->coo_kernel == 2 && A->coo_rb) {
+        const unsigned g = (unsigned)((A->coo_nrb + kThreads / 32 - 1) / (kThreads / 32));
+        launch_kernel(ep.pdl, spmv_coo_rb_kernel<VT, T>, g, kThreads, 0, s, A->nrows, A->ai, A->aj,
+                      static_cast<const VT*>(A->av), (const int32_t*)A->coo_rb, A->coo_nrb, x, y,
+                      (const CgState*)ep.st, ep.acc);
+        nch = 0;   // no carries
+    } else if (A->coo_kernel == 1) {
         const int chunk = A->coo_chunk == 512 ? 512 : kCooVecChunk;
         nch = (A->nnz + chunk - 1) / chunk;   // <= A->nchunks, the carry records allocated
         const unsigned g = (unsigned)((nch + kThreads / 32 - 1) / (kThreads / 32));

@@ -81,7 +81,8 @@ def test_split_spmv_equals_whole(mspv, orc, local_fmt, remote_fmt):
 
 
 CASES = [
-    ("coo_vec", "coo", "vec"), ("coo_seg", "coo", "seg"), ("csr", "csr", None), ("dia", "dia", None),
+    ("coo_rb", "coo", "rb"), ("coo_vec", "coo", "vec"), ("coo_seg", "coo", "seg"), ("csr", "csr", None),
+    ("dia", "dia", None),
 ]
 
 

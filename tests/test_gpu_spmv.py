@@ -170,11 +170,12 @@ def test_csr_every_kernel_choice(mspv, orc, vec, monkeypatch):
     assert_spmv_parity(L.spmv(dev(x)).cpu().numpy(), OL, x, orc)
 
 
-@pytest.mark.parametrize("kernel", ["seg", "vec", "vec512"])
+@pytest.mark.parametrize("kernel", ["seg", "vec", "vec512", "rb"])
 def test_coo_every_kernel_choice(mspv, orc, kernel, monkeypatch):
-    """Both COO kernels (lane-sequential 512-entry segments; run-vector 256-entry chunks) on
-    shapes that hit their edges: rows spanning lanes and chunks, a row covering many chunks,
-    empty rows before, between and after entries, partial last lanes and chunks, one entry."""
+    """Every COO kernel (lane-sequential 512-entry segments; run-vector 256-entry chunks; 8-row
+    blocks) on shapes that hit their edges: rows spanning lanes and chunks, a row covering many
+    chunks, empty rows before, between and after entries (whole empty row blocks), partial
+    last lanes and chunks, one entry."""
     monkeypatch.setenv("MSPV_COO_KERNEL", kernel[:3])
     monkeypatch.setenv("MSPV_COO_CHUNK", "512" if kernel == "vec512" else "256")
     rng = np.random.default_rng(31)
