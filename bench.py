@@ -275,7 +275,9 @@ def run_mspv(args, world, rank, local):
 
     # gpu launches of this library inside the timed region
     # COO: the row-block kernel alone (rows of at most 128 entries), else a chunked kernel + fix-up
-    coo_kernel = os.environ.get("MSPV_COO_KERNEL") or ("rb" if A.info["row_max"] <= 128 else "seg")
+    inf = A.info
+    coo_kernel = os.environ.get("MSPV_COO_KERNEL") or (
+        "seg" if inf["row_max"] > 128 else ("rb" if inf["nnz"] >= 4 * inf["nrows"] else "vec"))
     chunk = 512 if coo_kernel == "seg" else 256
     coo_launches = 1 if coo_kernel == "rb" else 1 + (1 if (nnz + chunk - 1) // chunk > 1 else 0)
     # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update

@@ -733,17 +733,20 @@ mspv_status split_columns(const mspv_matrix* A, int32_t c, cudaStream_t s, mspv_
     return MSPV_OK;
 }
 
-// COO kernel for the longest row: short rows (at most 128 entries) take the row-block
-// kernel (a warp per 8 consecutive rows, 4 lanes per row, chunks that never cut a row);
-// matrices with longer rows take the lane-sequential segment kernel, which keeps every lane
-// busy however the rows are cut. MSPV_COO_KERNEL=rb|vec|seg overrides (vec: the run-vector
-// kernel, fixed 256-entry chunks).
-int32_t choose_coo_kernel(int32_t row_max) {
+// COO kernel for the row lengths: short rows (at most 128 entries) take the row-block kernel
+// (a warp per 8 consecutive rows, 4 lanes per row, chunks that never cut a row) when rows
+// average at least 4 entries, and the run-vector kernel (fixed 256-entry chunks) when they are
+// sparser: the row-block kernel spends a warp on every 8 rows, empty or not (the remote part of
+// a process's matrix, ~95 % empty rows, took 3x longer). Longer rows take the lane-sequential
+// segment kernel, which keeps every lane busy however the rows are cut. MSPV_COO_KERNEL=
+// rb|vec|seg overrides.
+int32_t choose_coo_kernel(int32_t row_max, int64_t nnz, int32_t nrows) {
     const char* k = std::getenv("MSPV_COO_KERNEL");
     if (k && std::strcmp(k, "rb") == 0) return 2;
     if (k && std::strcmp(k, "vec") == 0) return 1;
     if (k && std::strcmp(k, "seg") == 0) return 0;
-    return row_max <= 128 ? 2 : 0;
+    if (row_max > 128) return 0;
+    return nnz >= 4 * (int64_t)nrows ? 2 : 1;
 }
 
 // First entry of every block of kCooRbRows rows in row-sorted COO (blocks past the last
@@ -765,7 +768,7 @@ __global__ void fill_i32_kernel(int32_t* __restrict__ v, int64_t n, int32_t valu
 
 mspv_status ensure_coo_carry(mspv_matrix* M, cudaStream_t s) {
     if (M->format != MSPV_COO || M->carry) return MSPV_OK;
-    M->coo_kernel = choose_coo_kernel(M->row_max);
+    M->coo_kernel = choose_coo_kernel(M->row_max, M->nnz, M->nrows);
     const char* ch = std::getenv("MSPV_COO_CHUNK");
     M->coo_chunk = (ch && std::atoi(ch) == 512) ? 512 : kCooVecChunk;
     M->nchunks = (M->nnz + kCooVecChunk - 1) / kCooVecChunk;

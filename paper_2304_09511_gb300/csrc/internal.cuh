@@ -294,7 +294,7 @@ int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen);
 mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s);
 mspv_status build_csr_long_rows(mspv_matrix* M, cudaStream_t s);
 int32_t choose_csr_block_kernel();   // MSPV_CSR_KERNEL=block selects CTA row blocks
-int32_t choose_coo_kernel(int32_t row_max);   // 2 row blocks, 1 run-vector, 0 lane-sequential segments
+int32_t choose_coo_kernel(int32_t row_max, int64_t nnz, int32_t nrows);   // 2 row blocks, 1 run-vector, 0 segments
 
 // cg.cu
 mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int32_t maxit,
