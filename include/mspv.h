@@ -55,7 +55,7 @@ typedef enum {
     MSPV_OK = 0,
     MSPV_EINVAL = 1,      /* bad argument: null pointer, negative size, index out of range */
     MSPV_ENOMEM = 2,      /* device allocation failed or exceeded MSPV_MAX_BYTES */
-    MSPV_ETOOBIG = 3,     /* DIA storage would exceed its fill cap, or nnz >= 2^31 */
+    MSPV_ETOOBIG = 3,     /* DIA storage would exceed its fill cap or 2^31 - 1 padded rows, or nnz >= 2^31 */
     MSPV_EFORMAT = 4,     /* operation not defined for this format (e.g. DIA of a non-square matrix) */
     MSPV_ECUDA = 5,       /* a CUDA runtime call failed; see mspv_last_error() */
     MSPV_ENOTCONV = 6,    /* CG reached its iteration limit above the tolerance */
@@ -103,7 +103,8 @@ MSPV_API mspv_status mspv_create_coo(int32_t nrows, int32_t ncols, int64_t nnz,
  *    npad = ceil(nrows / 32) * 32 and zeros in every slot outside the matrix or
  *    without an entry. Square matrices only (EFORMAT otherwise). ETOOBIG when
  *    ndiags * npad exceeds max(32 * nnz, 2^20) slots (DIA's storage blow-up on
- *    scattered patterns), or the MSPV_DIA_MAX_FILL override of the factor 32.
+ *    scattered patterns), or the MSPV_DIA_MAX_FILL override of the factor 32, and when npad
+ *    would exceed 2^31 - 1 (nrows > 2^31 - 32).
  *  - COO: a copy, possibly with another value type.
  * A may be COO or CSR; converting from DIA returns EFORMAT.
  */

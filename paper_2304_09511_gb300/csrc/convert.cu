@@ -572,6 +572,10 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
     if (A->nrows != A->ncols)
         return set_error(MSPV_EFORMAT, "convert: DIA needs a square matrix (got %d x %d)", A->nrows, A->ncols);
     const int32_t n = A->nrows;
+    const int64_t npad64 = ((int64_t)n + 31) / 32 * 32;   // checked before any workspace is allocated
+    if (npad64 > INT32_MAX)
+        return set_error(MSPV_ETOOBIG, "convert: %d rows padded to a multiple of 32 exceed 2^31 - 1", n);
+    const int32_t npad = (int32_t)npad64;
     const int64_t span = n > 0 ? 2 * (int64_t)n - 1 : 0;
     DevBuf flags, map, total;
     MSPV_TRY(flags.alloc(sizeof(int32_t) * (size_t)(span > 0 ? span : 1)));
@@ -586,7 +590,6 @@ mspv_status build_from(const mspv_matrix* A, int32_t format, int32_t vt, cudaStr
     int32_t nd = 0;
     MSPV_CUDA_TRY(cudaMemcpyAsync(&nd, total.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-    const int32_t npad = ((n + 31) / 32) * 32;
     const double slots = (double)nd * (double)npad;
     const double cap = dia_slot_cap(nnz);
     if (slots > cap)

@@ -1043,12 +1043,6 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
     const int32_t row_first = srow[0], row_last = srow[len - 1];
     const bool cont_prev = (row_before == row_first);
     const bool cont_next = (row_after == row_last);
-    // rows with no entries between consecutive runs (and before the first)
-    for (int i = threadIdx.x; i < nruns; i += kThreads) {
-        const int32_t r = srow[rs[i]];
-        const int32_t prev = (i > 0) ? srow[rs[i] - 1] : row_before;
-        for (int32_t z = prev + 1; z < r; ++z) zero_y(y, z, acc);
-    }
     reduce_runs<VT>(a_s, x_s, rs, nruns, [&](int i, T sum) {
         const int32_t r = srow[rs[i]];
         const bool to_head = (i == 0) && cont_prev;
@@ -1061,8 +1055,6 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_stage_kernel(
         carry[w].row_first = row_first;
         carry[w].row_last = row_last;
     }
-    if (s + len == nnz)   // empty rows after the last entry
-        for (int32_t z = row_last + 1 + threadIdx.x; z < nrows; z += kThreads) zero_y(y, z, acc);
 }
 
 // COO, run-vector kernel. Warp c takes the chunk of CHUNK (256 or 512) sorted entries
@@ -1113,8 +1105,6 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
             const int pos = nr + __popc(ballot & ((1u << lane) - 1u));
             rs[pos] = k;
             rrow[pos] = r;
-            if (r != prev)
-                for (int32_t z = prev + 1; z < r; ++z) zero_y(y, z, acc);   // empty rows in between
         }
         nr += __popc(ballot);
         carry_row = __shfl_sync(FULL, r, 31);
@@ -1147,8 +1137,6 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
         carry[c].row_first = rrow[0];
         carry[c].row_last = rrow[nr - 1];
     }
-    if (c0 + len == nnz)   // empty rows after the last entry
-        for (int32_t z = rrow[nr - 1] + 1 + lane; z < nrows; z += 32) zero_y(y, z, acc);
 }
 
 // COO, a warp per block of kCooRbRows consecutive rows. The block's entries [rb[b], rb[b+1])
@@ -1173,7 +1161,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t b = (int64_t)blockIdx.x * (kThreads / 32) + w;
     if (b >= nrb) return;   // whole warp
-    const int32_t row0 = (int32_t)(b * kCooRbRows);
+    const int64_t row0 = b * kCooRbRows;   // 64-bit: the last block may reach past 2^31 - 1
     const int64_t e0 = __ldg(rb + b);
     const int cnt = (int)(__ldg(rb + b + 1) - e0);
     int32_t* start = s_start[w];
@@ -1188,14 +1176,14 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
         const int k = q * 32 + lane;
         rv[q] = (k < cnt) ? __ldcs(ai + e0 + k) : INT_MAX;
     }
-    int32_t last = row0 - 1;   // row of the entry before the current 32
+    int32_t last = (int32_t)(row0 - 1);   // row of the entry before the current 32 (row0 <= nrows - 1)
 #pragma unroll
     for (int q = 0; q < kHeld; ++q) {
         const int k = q * 32 + lane;
         const int32_t r = rv[q];
         int32_t prev = __shfl_up_sync(FULL, r, 1);
         if (lane == 0) prev = last;
-        if (k < cnt && r != prev) start[r - row0] = k;
+        if (k < cnt && r != prev) start[(int)(r - row0)] = k;
         last = __shfl_sync(FULL, r, 31);
     }
     for (int k0 = kHeld * 32; k0 < cnt; k0 += 32) {
@@ -1203,12 +1191,12 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
         const int32_t r = (k < cnt) ? __ldcs(ai + e0 + k) : INT_MAX;
         int32_t prev = __shfl_up_sync(FULL, r, 1);
         if (lane == 0) prev = last;
-        if (k < cnt && r != prev) start[r - row0] = k;
+        if (k < cnt && r != prev) start[(int)(r - row0)] = k;
         last = __shfl_sync(FULL, r, 31);
     }
     __syncwarp();
     const int grp = lane >> 2, sub = lane & 3;
-    const int32_t row = row0 + grp;
+    const int64_t row = row0 + grp;
     const int bg = start[grp];
     int eg = cnt;   // the next row of the block that has entries starts where this one ends
     for (int g2 = grp + 1; g2 < kCooRbRows; ++g2)
@@ -1348,7 +1336,6 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
                             if (!closed) { head = sum; closed = true; }
                             else store_y(y, cur, sum, acc);
                         }
-                        for (int32_t z = cur + 1; z < r; ++z) zero_y(y, z, acc);   // empty rows
                         cur = r;
                         sum = T(0);
                     }
@@ -1396,8 +1383,6 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
         carry[c].row_first = chunk_first;
         carry[c].row_last = chunk_last;
     }
-    if (c0 + len == nnz)   // empty rows after the last entry
-        for (int32_t z = chunk_last + 1 + lane; z < nrows; z += 32) zero_y(y, z, acc);
 }
 
 template <typename T>
@@ -1761,6 +1746,11 @@ static void launch_coo_windows(int32_t nrows, int64_t nnz, const int32_t* ai, co
 template <typename VT, typename T>
 static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
     int64_t nch;
+    // The chunked kernels write only rows that have entries: rows without any are zeroed here,
+    // in parallel, before them (y = A x; for y += A x they stay as they are). The row-block
+    // kernel writes every row of its blocks itself.
+    if (!(A->coo_kernel == 2 && A->coo_rb) && !ep.acc && A->empty_rows > 0)   // a plain launch: waits for
+        fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, (int64_t)A->nrows);   // its predecessor
     if (A->coo_kernel == 2 && A->coo_rb) {
         const unsigned g = (unsigned)((A->coo_nrb + kThreads / 32 - 1) / (kThreads / 32));
         launch_kernel(ep.pdl, spmv_coo_rb_kernel<VT, T>, g, kThreads, 0, s, A->nrows, A->ai, A->aj,
@@ -1804,6 +1794,8 @@ mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const 
         return MSPV_OK;
     }
     const int64_t nwin = (nnz + kCooWindow - 1) / kCooWindow;
+    // rows without entries (unknown for raw triplets) are zeroed first; the kernel writes the others
+    fill_zero_kernel<double><<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows);
     launch_coo_windows<double, double>(nrows, nnz, ai, aj, av, x, y, carry, nwin, s, nullptr);
     MSPV_CUDA_TRY(cudaGetLastError());
     return MSPV_OK;

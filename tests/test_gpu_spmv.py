@@ -123,6 +123,31 @@ def test_banded_structure_and_spmv(mspv, orc, case, fmt):
     assert_spmv_parity(M.spmv(dev(x)).cpu().numpy(), O, x, orc)
 
 
+@pytest.mark.parametrize("kernel", ["rb", "vec", "seg"])
+@pytest.mark.parametrize("acc", [False, True])
+def test_coo_long_empty_gaps(mspv, orc, kernel, acc, monkeypatch):
+    """Ten million rows, five entries (first rows, the middle, the last row): the rows between
+    them are zeroed in parallel (y = A x) or left as they are (y += A x) by every COO kernel."""
+    monkeypatch.setenv("MSPV_COO_KERNEL", kernel)
+    n = 10_000_000
+    r = np.array([0, 0, 3, n // 2, n - 1], np.int32)
+    c = np.array([1, 5, 3, n - 7, 0], np.int32)
+    v = np.array([0.5, -2.0, 3.0, 1.25, -0.75])
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    x = torch.linspace(-1.0, 1.0, n, dtype=torch.float64, device="cuda")
+    y0 = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
+    y = y0.clone()
+    if acc:
+        A.spmv_add(x, y)
+    else:
+        A.spmv(x, y)
+    xh = x.cpu().numpy()
+    want = np.full(n, 7.0) if acc else np.zeros(n)
+    np.add.at(want, r, v * xh[c])
+    got = y.cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-15, atol=1e-15)
+
+
 @pytest.mark.parametrize("arith", ["f64", "f32", "bf16"])
 def test_dia_more_diagonals_than_shared_tables(mspv, orc, arith):
     """600 scattered diagonals (about 550 runs of consecutive offsets): past the 256 offsets and
