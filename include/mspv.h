@@ -137,7 +137,7 @@ MSPV_API mspv_status mspv_spmv(mspv_matrix_t A, const double* x, double* y, void
  * EBREAKDOWN (p.q <= 0 or non-finite alpha; x holds the last completed iterate).
  * Vector work runs on the device with device-resident scalars; the host polls a
  * convergence flag every MSPV_CG_CHECK_EVERY iterations (default 10; with tol <= 0, a fixed
- * count, all maxit iterations are launched before the one poll unless that variable is set);
+ * count, every 256 iterations unless that variable is set);
  * launches past convergence are no-ops, so results do not depend on that interval.
  * Workspace (3 vectors + reduction partials) is allocated once per handle.
  */

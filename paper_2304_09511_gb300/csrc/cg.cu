@@ -456,10 +456,11 @@ static int check_every() {
 }
 
 // Iterations launched between two polls of the stop flag: MSPV_CG_CHECK_EVERY when set, else
-// 10; a run with tol <= 0 has a fixed count (only a breakdown stops it early, and launches past
-// it are no-ops), so it is launched in one batch and the GPU is not drained to poll.
+// 10; a run with tol <= 0 has a fixed count (only a breakdown or an exactly zero residual stops
+// it early, and launches past that are no-ops), so it goes in batches of up to 256 and the GPU
+// is rarely drained to poll.
 static int32_t poll_batch(double tol, int32_t remaining) {
-    if (tol <= 0.0 && !std::getenv("MSPV_CG_CHECK_EVERY")) return remaining;
+    if (tol <= 0.0 && !std::getenv("MSPV_CG_CHECK_EVERY")) return std::min<int32_t>(256, remaining);
     return std::min<int32_t>(check_every(), remaining);
 }
 
