@@ -230,6 +230,25 @@ def test_reliable_updates_match_oracle(mspv, orc, vt, fmt):
     assert 1 <= res.outer_iters <= nu + 3
 
 
+@pytest.mark.parametrize("vt", ["f32", "bf16"])
+def test_reliable_updates_ragged_size(mspv, orc, vt):
+    """21^3 = 9,261 rows (not a multiple of the 4 or 8 rows a thread of the FP32 DIA kernel
+    owns, nor of the 32-row padding): reliable updates on DIA still reach the FP64 answer."""
+    g = 21
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 9)
+    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
+    D = A.convert("dia")
+    O = orc.coo_to_dia(orc.canonicalize(n, n, r, c, v))
+    b = orc.spmv(O, synth.uniform_x(n, 13) - 0.5)
+    res = D.cg_ru(A.convert("dia", vt), dev(b), tol=1e-10, maxit=2000)
+    assert res.converged and res.relres <= 1e-10
+    x = res.x.cpu().numpy()
+    assert np.linalg.norm(b - orc.spmv(O, x)) / np.linalg.norm(b) <= 1.5e-10
+    xo, st, _, _, _, _ = orc.cg(O, b, tol=1e-12, maxit=2000)
+    assert st == orc.OK and np.max(np.abs(x - xo)) <= 1e-8 * np.max(np.abs(xo))
+
+
 def test_reliable_updates_large_dia(mspv):
     """64^3 perturbed stencil (262,144 rows) in DIA: FP32 values take at most 5% more
     iterations than FP64 CG, BF16 values at most 40% more; both reach 1e-10."""
