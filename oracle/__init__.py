@@ -14,7 +14,9 @@ Functions and the passages they follow:
   round_values   FP32 / BF16 storage rounding (round to nearest even from FP64)
   cg             unpreconditioned CG as run in the paper's HPCG experiments (Sec. VI)
   cg_ir          FP64 iterative refinement around a low-precision inner CG (not in
-                 the paper; pinned only by its final FP64 residual)
+                 the paper; pinned by the dense stationary recursion
+                 x += Alo^-1 (b - A64 x) step by step, its contraction bound and its
+                 final FP64 residual)
   cg_ru          one low-precision CG with reliable updates of its residual from
                  FP64 (not in the paper; pinned by finite termination, by equality
                  with cg when both matrices are equal, and by its final residual)

@@ -361,6 +361,51 @@ def test_cg_ir_reaches_fp64_tolerance_with_bf16_values(orc):
     assert true <= 1e-10 and np.max(np.abs(x - 1)) < 1e-8
 
 
+def check_refinement_outer_steps(orc, vt="bf16"):
+    """Iterative refinement with exact inner solves is the stationary iteration
+    x_{k+1} = x_k + Alo^{-1} (b - A64 x_k). On a perturbed stencil small enough for dense
+    elimination, with the inner CG run to 1e-14, the oracle's k-th outer iterate must be
+    that recursion's (to cond * 1e-13), its reported residual the recursion's FP64 residual,
+    and each outer step must contract the residual by at most ||I - A64 Alo^{-1}||_2. The
+    first iterate is Alo^{-1} b, which differs from A64^{-1} b by the storage rounding, so an
+    inner solve on the FP64 matrix, a residual taken from the rounded matrix or a wrong sign
+    in the update each fail here."""
+    g = 5
+    n = g ** 3
+    r, c, v = synth.stencil27_perturbed(g, 3)
+    C = orc.coo_to_csr(orc.canonicalize(n, n, r, c, v))
+    Clo = orc.with_values(C, vt)
+    D = dense_of(n, n, orc.csr_to_coo(C).ai, C.aj, C.av)
+    Dlo = dense_of(n, n, orc.csr_to_coo(C).ai, C.aj, Clo.av)
+    assert not np.array_equal(D, Dlo)
+    cond = np.linalg.cond(Dlo)
+    contraction = np.linalg.norm(np.eye(n) - D @ np.linalg.inv(Dlo), 2)
+    assert contraction < 1.0
+    b = synth.uniform_x(n, 4) - 0.5
+    bnorm = np.linalg.norm(b)
+    xd = np.zeros(n)
+    prev = 1.0
+    for k in (1, 2, 3):
+        xd = xd + np.linalg.solve(Dlo, b - D @ xd)
+        want_rel = np.linalg.norm(b - D @ xd) / bnorm
+        x, st, outer, inner, rel = orc.cg_ir(C, Clo, b, tol=1e-300, inner_tol=1e-14,
+                                             max_outer=k, maxit_inner=5000)
+        assert st == orc.NOTCONV and outer == k and inner > 0
+        assert np.linalg.norm(x - xd) <= cond * 1e-13 * np.linalg.norm(xd)
+        assert abs(rel - want_rel) <= 1e-12
+        assert rel <= contraction * prev + 1e-12
+        prev = rel
+        if k == 1:
+            # the storage rounding is visible far above the tolerance
+            x64 = np.linalg.solve(D, b)
+            assert np.linalg.norm(x - x64) > 1e3 * cond * 1e-13 * np.linalg.norm(x64)
+
+
+@pytest.mark.parametrize("vt", ["bf16", "f32"])
+def test_cg_ir_outer_steps_follow_dense_refinement(orc, vt):
+    check_refinement_outer_steps(orc, vt)
+
+
 def test_cg_ru_iterates_match_exact_rational_cg(orc):
     """With both matrices equal, the replaced residual is the recursive one up to rounding,
     so reliable updates after every iteration (delta = 2) reproduce the textbook iterates
