@@ -737,9 +737,9 @@ mspv_status split_columns(const mspv_matrix* A, int32_t c, cudaStream_t s, mspv_
 }
 
 // COO kernel for the row lengths: short rows (at most 128 entries) take the row-block kernel
-// (a warp per 8 consecutive rows, 4 lanes per row, chunks that never cut a row) when rows
+// (a warp per 32 consecutive rows, 4 lanes per row, chunks that never cut a row) when rows
 // average at least 4 entries, and the run-vector kernel (fixed 256-entry chunks) when they are
-// sparser: the row-block kernel spends a warp on every 8 rows, empty or not (the remote part of
+// sparser: the row-block kernel spends a warp on every 32 rows, empty or not (the remote part of
 // a process's matrix, ~95 % empty rows, took 3x longer). Longer rows take the lane-sequential
 // segment kernel, which keeps every lane busy however the rows are cut. MSPV_COO_KERNEL=
 // rb|vec|seg overrides.

@@ -182,7 +182,7 @@ struct CooCarry {
 // staged in shared memory (16 B per entry, plus 4 B of row index for COO).
 constexpr int kCooWindow = 3072;    // staged COO kernel (allocation-free entry point)
 constexpr int kCooVecChunk = 256;   // run-vector COO kernel: entries per warp
-constexpr int kCooRbRows = 8;       // row-block COO kernel: rows per warp (4 lanes each)
+constexpr int kCooRbRows = 32;      // row-block COO kernel: rows per warp (4 lanes each)
 constexpr int kCsrWindow = 2560;     // a CTA takes the rows that start in its window
 
 // CG workspace, owned by a handle and grown on demand.

@@ -621,10 +621,100 @@ __device__ __forceinline__ T convert_value(VT v) {
     else return __uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);
 }
 
-// V lanes per row, lane-strided FMAs and a log2(V)-step shuffle reduction. V = 4 suits
-// short rows on GB300: a warp instruction still covers 8 rows x 32-byte segments
-// (coalesced enough), while the reduction costs 2 FP64 shuffle-adds per 8 rows. Rows
-// longer than long_len are skipped here and reduced by spmv_csr_long_kernel.
+// The FMA phase of the 32-row CSR and COO kernels. A warp owns 32 consecutive rows; lane
+// (grp, sub) = (lane / V, lane % V) keeps V partial sums, one for each of the rows R t + grp
+// (t < V, R = 32 / V rows per pass of the warp). The passes run one after another, each like a
+// V-lanes-per-row pass over R consecutive rows (lane-strided FMAs, R segments of V consecutive
+// values per load instruction), but the partial sums are not reduced per pass: a reduce-scatter
+// at the end joins the V lanes of every row. At each of its log2(V) steps a lane keeps half of
+// its partials, receives its partner's copy of that half and adds it, so lane (grp, sub) ends
+// with the whole sum of row R sub + grp after V - 1 FP64 adds. A shuffle-add reduction after every pass costs log2(V)
+// adds per pass, V log2(V) per 32 rows (8 against 3 for V = 4): on GB300's narrow FP64 pipe
+// those adds are a fifth of a 27-entry row's FMA instructions.
+// The matrix is read through the read-only path with normal cache priority: a row may start at
+// any entry, so a lane group's V values often straddle two 32-byte sectors and the same warp's
+// next load uses the rest. With streaming (evict-first) loads that remainder was often gone
+// from L1 and the kernels ran 1.2-1.3x slower (192^3 stencil); an evict-first hint for L2
+// alone was slower still inside the benchmark step.
+// bounds(t, s, len) gives the first entry and the length of row R t + grp (len 0: a row written
+// elsewhere); every lane calls it for every t outside divergent code, so it may shuffle.
+template <typename VT, typename T, int V, typename Bounds>
+__device__ __forceinline__ T rows32_sum(int sub, const int32_t* __restrict__ aj, const VT* __restrict__ av,
+                                        const T* __restrict__ x, Bounds bounds) {
+    const unsigned FULL = 0xffffffffu;
+    T part[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+        int32_t s0, len;
+        bounds(t, s0, len);
+        T acc = T(0);
+        for (int32_t off = sub; off < len; off += V) {
+            const int64_t j = (int64_t)s0 + off;
+            acc = fma_t(convert_value<T>(__ldg(av + j)), __ldg(x + __ldg(aj + j)), acc);
+        }
+        part[t] = acc;
+    }
+#pragma unroll
+    for (int h = V / 2; h >= 1; h >>= 1) {
+        const bool upper = (sub & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T give = upper ? part[i] : part[i + h];
+            const T keep = upper ? part[i + h] : part[i];
+            part[i] = keep + __shfl_xor_sync(FULL, give, h);
+        }
+    }
+    return part[0];
+}
+
+// CSR with V lanes per row (V = 1, 2, 4, 8), a warp per 32 consecutive rows (rows32_sum).
+// The warp's 33 row pointers come from one coalesced load spread by shuffles. Rows longer
+// than long_len are skipped here and reduced by spmv_csr_long_kernel. Lane (grp, sub) writes
+// row R sub + grp of the warp: the 32 stores of a warp land in one 256-byte span.
+template <typename VT, typename T, int V, bool STRIDE>
+__global__ void __launch_bounds__(kThreads) spmv_csr_rows32_kernel(
+    int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
+    const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y, int32_t long_len,
+    DotEpilogue ep) {
+    static_assert(V == 1 || V == 2 || V == 4 || V == 8, "lanes per row");
+    constexpr int R = 32 / V;
+    pdl_wait();
+    pdl_trigger();
+    if (ep.st && ep.st->done) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, sub = lane & (V - 1), grp = lane / V;
+    const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    // Inside CG (STRIDE) the grid is capped so the scalar kernels have fewer partials to sum,
+    // and the warps stride over the rows, 32 rows per warp and pass.
+    const int64_t step = STRIDE ? (int64_t)gridDim.x * kThreads : 0;
+    T dot = T(0);
+    for (int64_t base = warp * 32; base < nrows; base += step) {
+        const int32_t p = __ldg(irp + min(base + lane, (int64_t)nrows));
+        const int32_t pend = __ldg(irp + min(base + 32, (int64_t)nrows));
+        const T sum = rows32_sum<VT, T, V>(sub, aj, av, x, [=](int t, int32_t& s0, int32_t& len) {
+            const int r = R * t + grp;
+            const int32_t a = __shfl_sync(FULL, p, r);
+            const int32_t b1 = __shfl_sync(FULL, p, (r + 1) & 31);
+            const int32_t l = (r == 31 ? pend : b1) - a;
+            s0 = a;
+            len = l > long_len ? 0 : l;
+        });
+        const int rr = R * sub + grp;
+        const int32_t a = __shfl_sync(FULL, p, rr);
+        const int32_t b1 = __shfl_sync(FULL, p, (rr + 1) & 31);
+        const int64_t row = base + rr;
+        if (row < nrows && (rr == 31 ? pend : b1) - a <= long_len) {
+            store_y(y, row, sum, ep.acc);
+            if (ep.st) dot = fma_t(__ldg(x + row), sum, dot);
+        }
+        if (!STRIDE) break;
+    }
+    if (ep.st) finish_dot(dot, ep);
+}
+
+// V lanes per row for wide rows (V = 16, 32), lane-strided FMAs and a log2(V)-step shuffle
+// reduction per pass of 32 / V rows. Rows longer than long_len are skipped here and reduced by
+// spmv_csr_long_kernel.
 template <typename VT, typename T, int V, bool STRIDE>
 __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
     int32_t nrows, const int32_t* __restrict__ irp, const int32_t* __restrict__ aj,
@@ -1139,20 +1229,23 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
     }
 }
 
-// COO, a warp per block of kCooRbRows consecutive rows. The block's entries [rb[b], rb[b+1])
-// come from a table built with the handle (one int per 8 rows); a row never crosses a block,
-// so there are no carries and no fix-up pass. The warp reads the block's row indices 32 at a
-// time, marks where each row starts (ballot over row changes) in shared memory, then 4 lanes
-// per row (one row per lane group, the whole block in one pass) accumulate lane-strided FMAs
-// and join them with two shuffle-adds: the CSR V = 4 instruction count with every row index
-// still read. Rows of the block without entries are written as 0 (left as they are for
-// y += A x). For rows of at most 128 entries (longer ones take the segment kernel).
+// COO, a warp per block of kCooRbRows = 32 consecutive rows. The block's entries
+// [rb[b], rb[b+1]) come from a table built with the handle (one int per 32 rows); a row never
+// crosses a block, so there are no carries and no fix-up pass. The warp reads the block's row
+// indices in 16-byte groups (lane l the l-th group of each 128-entry stretch, every group of
+// the block in flight at once for rows of stencil length), marks where each row starts (a row
+// change against the previous entry) in shared memory, finds where each row ends by a suffix
+// minimum over the next rows' starts, and then runs the FMA phase of the 32-row CSR kernel
+// (rows32_sum, 4 lanes per row, reduce-scatter). Rows of the block without entries are
+// written as 0 (left as they are for y += A x). For rows of at most 128 entries (longer ones
+// take the segment kernel).
 template <typename VT, typename T>
 __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
-    int32_t nrows, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj, const VT* __restrict__ av,
-    const int32_t* __restrict__ rb, int64_t nrb, const T* __restrict__ x, T* __restrict__ y, const CgState* st,
-    bool acc) {
-    static_assert(kCooRbRows * 4 == 32, "one warp: kCooRbRows rows of 4 lanes");
+    int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
+    const VT* __restrict__ av, const int32_t* __restrict__ rb, int64_t nrb, const T* __restrict__ x,
+    T* __restrict__ y, const CgState* st, bool acc) {
+    static_assert(kCooRbRows == 32, "a warp per block of 32 rows");
+    constexpr int V = 4, R = 32 / V;
     pdl_wait();
     pdl_trigger();
     if (st && st->done) return;
@@ -1163,57 +1256,67 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
     if (b >= nrb) return;   // whole warp
     const int64_t row0 = b * kCooRbRows;   // 64-bit: the last block may reach past 2^31 - 1
     const int64_t e0 = __ldg(rb + b);
-    const int cnt = (int)(__ldg(rb + b + 1) - e0);
+    const int64_t e1 = __ldg(rb + b + 1);
+    const int cnt = (int)(e1 - e0);
     int32_t* start = s_start[w];
-    if (lane < kCooRbRows) start[lane] = -1;
+    start[lane] = -1;
     __syncwarp();
-    // The first 256 row indices are loaded together (8 independent loads per lane, the whole
-    // block of 8 stencil-like rows), the rest 32 at a time.
-    constexpr int kHeld = 8;
-    int32_t rv[kHeld];
+    // 16-byte groups from the multiple of 4 at or below e0; entries outside [e0, e1) are read
+    // (when below nnz) but not marked. ai's allocation starts 256-byte aligned.
+    const int64_t a0 = e0 & ~(int64_t)3;
+    constexpr int kHeld = 4;   // groups loaded together: 512 entries (two rounds for 32 stencil rows)
+    int32_t last = (int32_t)(row0 - 1);   // the row before the first group (a row below the block)
+    for (int64_t g0 = a0; g0 < e1; g0 += 128 * kHeld) {
+        int4 v[kHeld];
 #pragma unroll
-    for (int q = 0; q < kHeld; ++q) {
-        const int k = q * 32 + lane;
-        rv[q] = (k < cnt) ? __ldcs(ai + e0 + k) : INT_MAX;
-    }
-    int32_t last = (int32_t)(row0 - 1);   // row of the entry before the current 32 (row0 <= nrows - 1)
-#pragma unroll
-    for (int q = 0; q < kHeld; ++q) {
-        const int k = q * 32 + lane;
-        const int32_t r = rv[q];
-        int32_t prev = __shfl_up_sync(FULL, r, 1);
-        if (lane == 0) prev = last;
-        if (k < cnt && r != prev) start[(int)(r - row0)] = k;
-        last = __shfl_sync(FULL, r, 31);
-    }
-    for (int k0 = kHeld * 32; k0 < cnt; k0 += 32) {
-        const int k = k0 + lane;
-        const int32_t r = (k < cnt) ? __ldcs(ai + e0 + k) : INT_MAX;
-        int32_t prev = __shfl_up_sync(FULL, r, 1);
-        if (lane == 0) prev = last;
-        if (k < cnt && r != prev) start[(int)(r - row0)] = k;
-        last = __shfl_sync(FULL, r, 31);
-    }
-    __syncwarp();
-    const int grp = lane >> 2, sub = lane & 3;
-    const int64_t row = row0 + grp;
-    const int bg = start[grp];
-    int eg = cnt;   // the next row of the block that has entries starts where this one ends
-    for (int g2 = grp + 1; g2 < kCooRbRows; ++g2)
-        if (start[g2] >= 0) {
-            eg = start[g2];
-            break;
+        for (int q = 0; q < kHeld; ++q) {
+            const int64_t g = g0 + 128 * q + 4 * lane;
+            if (g + 3 < nnz) {
+                v[q] = __ldg(reinterpret_cast<const int4*>(ai + g));
+            } else {
+                v[q].x = g < nnz ? __ldg(ai + g) : INT_MAX;
+                v[q].y = g + 1 < nnz ? __ldg(ai + g + 1) : INT_MAX;
+                v[q].z = g + 2 < nnz ? __ldg(ai + g + 2) : INT_MAX;
+                v[q].w = INT_MAX;
+            }
         }
-    T sum = T(0);
-    if (bg >= 0) {
-#pragma unroll 4
-        for (int j = bg + sub; j < eg; j += 4)
-            sum = fma_t(convert_value<T>(__ldcs(av + e0 + j)), __ldg(x + __ldcs(aj + e0 + j)), sum);
+#pragma unroll
+        for (int q = 0; q < kHeld; ++q) {
+            const int64_t g = g0 + 128 * q + 4 * lane;
+            int32_t prev = __shfl_up_sync(FULL, v[q].w, 1);
+            if (lane == 0) prev = last;
+            last = __shfl_sync(FULL, v[q].w, 31);
+            const int32_t r[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int32_t pr = c == 0 ? prev : r[c - 1];
+                if (g + c >= e0 && g + c < e1 && r[c] != pr) start[(int)(r[c] - row0)] = (int)(g + c - e0);
+            }
+        }
     }
-    sum += __shfl_xor_sync(FULL, sum, 1);
-    sum += __shfl_xor_sync(FULL, sum, 2);
-    if (sub == 0 && row < nrows) {
-        if (bg >= 0) store_y(y, row, sum, acc);
+    __syncwarp();
+    // row (row0 + lane): its first entry (block-relative) and length; an empty row's end is the
+    // next nonempty row's start, the minimum of the starts of the rows after it (or cnt)
+    const int my = start[lane];
+    int nxt = __shfl_down_sync(FULL, my >= 0 ? my : cnt, 1);
+    if (lane == 31) nxt = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_down_sync(FULL, nxt, o);
+        if (lane + o < 32) nxt = min(nxt, t);
+    }
+    const int32_t mylen = my >= 0 ? nxt - my : 0;
+    const int sub = lane & (V - 1);
+    const T sum = rows32_sum<VT, T, V>(sub, aj, av, x, [=](int t, int32_t& s0, int32_t& len) {
+        const int r = R * t + lane / V;
+        s0 = (int32_t)e0 + __shfl_sync(FULL, my, r);
+        len = __shfl_sync(FULL, mylen, r);
+    });
+    const int rr = R * sub + lane / V;
+    const bool has = __shfl_sync(FULL, mylen, rr) > 0;
+    const int64_t row = row0 + rr;
+    if (row < nrows) {
+        if (has) store_y(y, row, sum, acc);
         else zero_y(y, row, acc);
     }
 }
@@ -1664,11 +1767,13 @@ static int64_t csr_warp_grid(int32_t nrows) {
     return g < 1 ? 1 : g;
 }
 
-// CTAs of the V-lane kernel; with a dot-product epilogue (inside CG) at most two waves of
-// 8 CTAs per SM, each group of V lanes striding over the rows.
+// CTAs of the V-lane kernels (a CTA covers kThreads rows for V <= 8, kThreads / V rows for
+// wider rows); with a dot-product epilogue (inside CG) at most two waves of 8 CTAs per SM, the
+// warps striding over the rows.
 constexpr int64_t kCsrCgGridCap = (int64_t)kNumSMs * 8 * 2;
 static int64_t csr_vector_grid(const mspv_matrix* A, bool capped) {
-    int64_t g = ((int64_t)A->nrows * A->csr_vector + kThreads - 1) / kThreads;
+    const int64_t lanes_per_row = A->csr_vector <= 8 ? 1 : A->csr_vector;
+    int64_t g = ((int64_t)A->nrows * lanes_per_row + kThreads - 1) / kThreads;
     if (capped && g > kCsrCgGridCap) g = kCsrCgGridCap;
     return g < 1 ? 1 : g;
 }
@@ -1707,23 +1812,23 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     const bool capped = ep.partials != nullptr;
     const unsigned grid = (unsigned)csr_vector_grid(A, capped);
     const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
-#define MSPV_CSR_CASE(VV)                                                                      \
+#define MSPV_CSR_CASE(VV, KERNEL)                                                              \
     case VV:                                                                                   \
         if (capped)                                                                            \
-            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, true>, grid, kThreads, 0, s, \
+            launch_kernel(ep.pdl, KERNEL<VT, T, VV, true>, grid, kThreads, 0, s,               \
                           A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                    \
         else                                                                                   \
-            launch_kernel(ep.pdl, spmv_csr_vector_kernel<VT, T, VV, false>, grid, kThreads, 0, s, \
+            launch_kernel(ep.pdl, KERNEL<VT, T, VV, false>, grid, kThreads, 0, s,              \
                           A->nrows, A->irp, A->aj, av, x, y, long_len, ep);                    \
         break;
     switch (V) {
-        MSPV_CSR_CASE(1)
-        MSPV_CSR_CASE(2)
-        MSPV_CSR_CASE(4)
-        MSPV_CSR_CASE(8)
-        MSPV_CSR_CASE(16)
+        MSPV_CSR_CASE(1, spmv_csr_rows32_kernel)
+        MSPV_CSR_CASE(2, spmv_csr_rows32_kernel)
+        MSPV_CSR_CASE(4, spmv_csr_rows32_kernel)
+        MSPV_CSR_CASE(8, spmv_csr_rows32_kernel)
+        MSPV_CSR_CASE(16, spmv_csr_vector_kernel)
         default:
-        MSPV_CSR_CASE(32)
+        MSPV_CSR_CASE(32, spmv_csr_vector_kernel)
     }
 #undef MSPV_CSR_CASE
     if (A->nlong > 0) {
@@ -1753,7 +1858,7 @@ static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, (int64_t)A->nrows);   // its predecessor
     if (A->coo_kernel == 2 && A->coo_rb) {
         const unsigned g = (unsigned)((A->coo_nrb + kThreads / 32 - 1) / (kThreads / 32));
-        launch_kernel(ep.pdl, spmv_coo_rb_kernel<VT, T>, g, kThreads, 0, s, A->nrows, A->ai, A->aj,
+        launch_kernel(ep.pdl, spmv_coo_rb_kernel<VT, T>, g, kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj,
                       static_cast<const VT*>(A->av), (const int32_t*)A->coo_rb, A->coo_nrb, x, y,
                       (const CgState*)ep.st, ep.acc);
         nch = 0;   // no carries
