@@ -193,7 +193,9 @@ MSPV_API mspv_status mspv_cg_solve_ir(mspv_matrix_t A64, mspv_matrix_t Alo, cons
  * returns ETOOBIG. EINVAL for an index outside the shape or decreasing rows (checked on
  * the device; the call synchronises `stream` once to read the check). The first call on
  * a device looks up the array's device address (call it once before any stream
- * capture). All calls share the array: calls that overlap on the GPU race on it.
+ * capture) and keeps it for the life of the process: after cudaDeviceReset, which unloads
+ * the library's device code, this entry point must not be called again in that process.
+ * All calls share the array: calls that overlap on the GPU race on it.
  */
 MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t ncols, int64_t nnz,
                                            const int32_t* rows, const int32_t* cols,
@@ -333,15 +335,6 @@ MSPV_API const char* mspv_status_string(mspv_status s);
  * slices). Exposed for tests and tuning.
  */
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max);
-
-/*
- * Device-side wait status (host call, synchronous with the device). The DIA SpMV that streams
- * its operands with bulk asynchronous copies bounds every wait on a copy; a wait that runs out
- * (not expected on a healthy device) leaves that SpMV's y incomplete and is recorded on the
- * device. Returns ECUDA once that has happened in this process (with a message), else OK.
- * The CG solvers check it before they return.
- */
-MSPV_API mspv_status mspv_device_status(void);
 
 /* Library version, as MAJOR * 10000 + MINOR * 100 + PATCH. */
 MSPV_API int32_t mspv_version(void);

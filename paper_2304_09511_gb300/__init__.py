@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import MspvError, FORMATS, VALUE_TYPES, load
 
-__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "device_status", "stream_handle",
+__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "stream_handle",
            "spmv_coo_noalloc", "selector_train", "selector_predict", "NUM_FEATURES",
            "SELECTOR_PARAMS"]
 
@@ -65,11 +65,6 @@ def spmv_coo_noalloc(nrows: int, ncols: int, rows, cols, vals, x, y, stream=None
 
 def csr_vector_width(row_mean: float, row_std: float = 0.0, row_max: int = 0) -> int:
     return int(load().mspv_csr_vector_width(row_mean, row_std, row_max))
-
-
-def device_status() -> None:
-    """Raises MspvError if a bounded device-side wait (bulk-copy DIA SpMV) has timed out."""
-    _lib.check(load().mspv_device_status())
 
 
 @dataclass

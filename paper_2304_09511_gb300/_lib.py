@@ -53,7 +53,6 @@ SIGNATURES = {
     "mspv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mspv_csr_vector_width": (i32, [dbl, dbl, i32]),
     "mspv_version": (i32, []),
-    "mspv_device_status": (i32, []),
     "mspv_spmv_add": (i32, [vp, vp, vp, vp]),
     "mspv_spmv_f32": (i32, [vp, vp, vp, vp]),
     "mspv_split_columns": (i32, [vp, i32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),

@@ -1,6 +1,7 @@
 // C-ABI entry points of libmspv.so (declared in include/mspv.h): argument checks,
 // device-memory accounting, error strings, and dispatch into the converters, the
 // SpMV kernels and the CG solvers. No exception leaves this file.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -79,6 +80,28 @@ void dev_free(void* p, size_t) {
     cudaFree(p);
 }
 
+// ---------------------------------------------------------------------------
+// SM count of the current device, cached per device ordinal
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+static std::atomic<int> g_sms[kMaxDevices];
+
+int num_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 152;   // GB300's count; only reached without a usable device
+    }
+    int v = g_sms[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        v = 152;
+    }
+    g_sms[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 }  // namespace mspv
 
 using namespace mspv;
@@ -114,12 +137,6 @@ MSPV_API const char* mspv_status_string(mspv_status s) {
 }
 
 MSPV_API int32_t mspv_version(void) { return 100; }
-
-MSPV_API mspv_status mspv_device_status(void) {
-    MSPV_GUARD_BEGIN
-    return check_device_fault();
-    MSPV_GUARD_END
-}
 
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max) {
     return choose_csr_vector(row_mean, row_std, row_max);

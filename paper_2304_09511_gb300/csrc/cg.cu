@@ -27,7 +27,7 @@ namespace mspv {
 
 static int64_t vec_grid(int64_t n) {   // upper bound of every wave_grid() (partials sizing)
     int64_t b = (n + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)kNumSMs * 8;
+    const int64_t cap = (int64_t)num_sms() * 8;
     if (b > cap) b = cap;
     return b < 1 ? 1 : b;
 }
@@ -42,7 +42,7 @@ static int64_t wave_grid(int64_t n) {
         return b;
     }();
     int64_t g = (n + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)kNumSMs * per_sm;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
     if (g > cap) g = cap;
     return g < 1 ? 1 : g;
 }
@@ -538,7 +538,6 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
         cg_update_kernel, cg_pupdate_kernel, Gu, Gp));
     if (iters) *iters = hst->iters;
     if (relres) *relres = std::sqrt(hst->rho) / hst->bnorm;
-    MSPV_TRY(check_device_fault());
     switch (hst->phase) {
         case CG_CONVERGED:
             return MSPV_OK;
@@ -578,7 +577,6 @@ static mspv_status cg_solve_f32(mspv_matrix* A, const float* b32, float* x32, do
         [&](const float* pp, float* qq, DotEpilogue ep) { return launch_spmv_f32(A, pp, qq, s, ep); },
         cgf_update_kernel, cgf_pupdate_kernel, Gu, Gp));
     *iters = hst->iters;
-    MSPV_TRY(check_device_fault());
     if (hst->phase == CG_BREAKDOWN)
         return set_error(MSPV_EBREAKDOWN, "cg (fp32 inner): breakdown at iteration %d", hst->iters);
     return MSPV_OK;
@@ -660,11 +658,6 @@ static mspv_status cg_solve_ru(mspv_matrix* A64, mspv_matrix* Alo, const double*
                 Alo, y32, w.rf, w.pf, w.qf, maxit - done, s,
                 [&](const float* pp, float* qq, DotEpilogue ep) { return launch_spmv_f32(Alo, pp, qq, s, ep); },
                 cgf_update_kernel, cgf_pupdate_kernel, Gu, Gp, done));
-        if (hst->phase == CG_FAULT) {
-            result = check_device_fault();
-            if (result == MSPV_OK) result = set_error(MSPV_ECUDA, "cg (reliable updates): device fault");
-            break;
-        }
         if (hst->phase == CG_BREAKDOWN) {
             result = set_error(MSPV_EBREAKDOWN, "cg (reliable updates): breakdown at FP32 iteration %d", hst->iters);
             break;
@@ -686,7 +679,6 @@ static mspv_status cg_solve_ru(mspv_matrix* A64, mspv_matrix* Alo, const double*
     if (iters) *iters = done;
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-    if (result != MSPV_ECUDA) MSPV_TRY(check_device_fault());
     if (result == MSPV_ENOTCONV)
         return set_error(MSPV_ENOTCONV, "cg (reliable updates): %d FP32 iterations, %d updates, residual %g above %g",
                          done, nupd, relres ? *relres : 0.0, tol);

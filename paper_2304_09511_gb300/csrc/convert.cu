@@ -255,7 +255,7 @@ __global__ void coalesce_kernel(const uint64_t* __restrict__ keys, const int32_t
 static unsigned grid_for(int64_t m, int per_thread = 1) {
     int64_t b = (m + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
     if (b < 1) b = 1;
-    if (b > (int64_t)kNumSMs * 64) b = (int64_t)kNumSMs * 64;   // grid-stride beyond this
+    if (b > (int64_t)num_sms() * 64) b = (int64_t)num_sms() * 64;   // grid-stride beyond this
     return (unsigned)b;
 }
 

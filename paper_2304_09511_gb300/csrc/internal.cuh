@@ -12,7 +12,9 @@
 namespace mspv {
 
 constexpr int kThreads = 256;       // threads per CTA for every kernel here
-constexpr int kNumSMs = 152;        // GB300: 2 dies x 76 SMs
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount; 152 on
+// GB300), read once per device and cached. Grid caps are multiples of it.
+int num_sms();
 
 // ---------------------------------------------------------------------------
 // errors
@@ -108,7 +110,7 @@ __device__ __forceinline__ double widen(__nv_bfloat16 v) {
 // ---------------------------------------------------------------------------
 // CG device state: scalars live on the device so the loop needs no host sync.
 // ---------------------------------------------------------------------------
-enum CgPhase : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3, CG_FAULT = 4 };
+enum CgPhase : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
 
 struct CgState {
     double rho;      // r.r of the current residual
@@ -285,7 +287,6 @@ mspv_status launch_spmv(const mspv_matrix* A, const double* x, double* y, cudaSt
 mspv_status launch_spmv_f32(const mspv_matrix* A, const float* x, float* y, cudaStream_t s,
                             DotEpilogue ep);
 int64_t spmv_partials_count(const mspv_matrix* A, bool f32);   // CTAs of the fused-dot launch
-mspv_status check_device_fault();   // ECUDA once a bounded device wait has timed out (synchronous)
 int64_t spmv_partials_needed(const mspv_matrix* A);   // the larger of the FP64 and FP32 counts
 mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* aj,
                            const double* av, const double* x, double* y, CooCarry* carry,

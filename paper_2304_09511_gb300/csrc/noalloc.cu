@@ -32,7 +32,9 @@ static std::mutex g_noalloc_mu;
 static NoAllocScratch* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached for the life of the process. cudaDeviceReset unloads
+// the module and would leave the cached address stale: the entry point is documented as not
+// callable after a device reset.
 static mspv_status noalloc_scratch(NoAllocScratch** out) {
     int dev = 0;
     MSPV_CUDA_TRY(cudaGetDevice(&dev));
@@ -87,7 +89,7 @@ extern "C" MSPV_API mspv_status mspv_spmv_coo_noalloc(int32_t nrows, int32_t nco
             // the flags keep the previous call's contents: clear them first
             MSPV_CUDA_TRY(cudaMemsetAsync(S->flags, 0, sizeof(S->flags), s));
             int64_t grid = (nnz + kThreads - 1) / kThreads;
-            if (grid > (int64_t)kNumSMs * 8) grid = (int64_t)kNumSMs * 8;
+            if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;
             noalloc_check_kernel<<<(unsigned)grid, kThreads, 0, s>>>(rows, cols, nnz, nrows, ncols, S->flags);
             MSPV_CUDA_TRY(cudaGetLastError());
             int32_t hflags[4] = {0, 0, 0, 0};

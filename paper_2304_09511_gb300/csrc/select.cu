@@ -61,7 +61,7 @@ __global__ void count_flags_kernel(const uint8_t* __restrict__ flags, int64_t m,
 
 static unsigned grid_cap(int64_t m) {
     int64_t g = (m + kThreads - 1) / kThreads;
-    if (g > (int64_t)kNumSMs * 16) g = (int64_t)kNumSMs * 16;
+    if (g > (int64_t)num_sms() * 16) g = (int64_t)num_sms() * 16;
     return (unsigned)(g < 1 ? 1 : g);
 }
 

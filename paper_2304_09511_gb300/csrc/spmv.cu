@@ -16,22 +16,22 @@
 //      The FP32-arithmetic kernel reads one x window per run of consecutive offsets, at
 //      4 rows per thread for FP32 values and 8 (one 16-byte value load per diagonal,
 //      128-thread CTAs) for BF16 values.
-//      A bulk-copy variant (opt-in, MSPV_DIA_BULK=1; measured slower, see dia_bulk_enabled):
-//      one persistent CTA per SM, each strip's diagonal slices and per-run x slices brought
-//      into a multi-stage shared-memory ring by bulk asynchronous copies (TMA engine,
-//      mbarrier byte counts), the FMAs reading shared memory, the same per-row FMA order.
 //  CSR (Algorithm 2): V lanes per row (V = 4 for short rows, chosen from the row-length
-//      statistics), lane-strided FMAs and a log2(V)-step shuffle reduction; rows longer
-//      than 32 V entries are listed at conversion and reduced by one CTA each. Inside CG
-//      the grid is capped and the row groups stride. Kernels that stage values and
-//      gathered x through shared memory (warp slices, CTA row blocks) are selectable.
-//  COO (Algorithm 1): rows of at most 128 entries take the run-vector kernel (a warp per
-//      256 sorted entries: ballot-compacted run starts, then 4 lanes per run); longer
-//      rows the lane-sequential segment kernel (16 entries per lane summed in order, a
-//      segmented scan joins rows across lanes) -- both forms of the paper's SVE COO idea
-//      of reducing runs of equal row index. Runs cut by a chunk edge leave partial sums in
-//      a carry record that a fix-up pass adds in chunk order. A staged window kernel
-//      serves the allocation-free entry point.
+//      statistics). Up to V = 8 a warp owns 32 rows, runs V passes of 32 / V rows with
+//      lane-strided FMAs and joins the passes' partial sums with one reduce-scatter
+//      (V - 1 FP64 adds per lane); wider rows take a log2(V)-step shuffle reduction per
+//      pass. Rows longer than 32 V entries are listed at conversion and reduced by one CTA
+//      each. Inside CG the grid is capped and the warps stride. Kernels that stage values
+//      and gathered x through shared memory (warp slices, CTA row blocks) are selectable.
+//  COO (Algorithm 1): rows of at most 128 entries, at least 4 per row on average, take the
+//      row-block kernel (a warp per 32 rows, whose entries a table of block starts gives;
+//      row starts marked from the row indices, then the CSR kernel's FMA phase); sparser
+//      short rows the run-vector kernel (a warp per 256 sorted entries: ballot-compacted run
+//      starts, then 4 lanes per run); longer rows the lane-sequential segment kernel (16
+//      entries per lane summed in order, a segmented scan joins rows across lanes) -- forms
+//      of the paper's SVE COO idea of reducing runs of equal row index. Runs cut by a chunk
+//      edge leave partial sums in a carry record that a fix-up pass adds in chunk order. A
+//      staged window kernel serves the allocation-free entry point.
 // No floating-point atomics anywhere: y is bit-identical run to run. Inside CG each
 // SpMV kernel writes its CTA's partial of p.q (DotEpilogue); the partials are summed in
 // index order by a one-CTA kernel. store_y is the single place a row of y is written
@@ -326,289 +326,6 @@ __global__ void __launch_bounds__(DiaF32Shape<VT>::NT) spmv_dia_f32_kernel(
             }
     }
     if (ep.st) finish_dot_nt<float, NT>(d, ep);
-}
-
-// ---------------------------------------------------------------------------
-// DIA fed by bulk asynchronous copies (the TMA engine), persistent CTAs
-// ---------------------------------------------------------------------------
-// One CTA per SM walks the strips blockIdx.x, blockIdx.x + gridDim.x, ... of R = NT * RPT
-// rows. For each strip one thread issues bulk copies (cp.async.bulk, completion counted in
-// bytes on an mbarrier) of the strip's slice of every diagonal of AV and of one x slice per
-// run of consecutive offsets into a shared-memory stage; `stages` stages are in flight, so
-// the DRAM stream of AV runs ahead of the arithmetic and the FMAs take their operands from
-// shared memory instead of waiting on global loads. Strips whose x slices would leave
-// [0, n) (the first and last few) or whose rows end past n are computed from global memory
-// with bounds checks instead. Either way each row's FMAs run over the diagonals in storage
-// order, so a row's sum is the same as in spmv_dia_kernel / spmv_dia_f32_kernel.
-// Every wait is bounded: on a time-out the kernel records it in *fault, waits (again
-// bounded) for its copies in flight and returns.
-constexpr int kBulkMaxDiags = 32;
-constexpr int kBulkMaxRuns = 32;
-constexpr int kBulkMaxStages = 4;
-constexpr uint32_t kBulkWaitTries = 1u << 22;
-
-__device__ unsigned int g_dia_bulk_fault;   // nonzero once a bulk-copy wait timed out
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        "  .reg .pred p;\n"
-        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "  selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase with the given parity; false after kBulkWaitTries polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t k = 0; k < kBulkWaitTries; ++k)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-// The same with an L2 eviction-priority hint (the matrix is streamed once: evict first, so
-// that the x slices, which nine strips' worth of runs re-read, stay in L2).
-__device__ __forceinline__ void bulk_copy_g2s_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    uint64_t policy;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
-        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
-        : "memory");
-}
-// Orders this thread's earlier generic-proxy accesses to shared memory before its later
-// async-proxy ones (a stage the CTA has finished reading is refilled by bulk copies).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-mspv_status check_device_fault() {
-    unsigned int f = 0;
-    MSPV_CUDA_TRY(cudaMemcpyFromSymbol(&f, g_dia_bulk_fault, sizeof(f)));
-    if (f) return set_error(MSPV_ECUDA, "a bulk-copy wait in the DIA SpMV timed out (results incomplete)");
-    return MSPV_OK;
-}
-
-// The stage layout of a strip: AV slices [ndiags][R] then x slices [nruns][XL].
-template <typename VT, typename T, int R>
-struct BulkLayout {
-    static constexpr int A = 16 / (int)sizeof(T);   // x elements per 16 bytes
-    static constexpr int XL = R + 2 * A;             // x slice: R rows + run shift (<= A - 1 + 2)
-    __host__ __device__ static size_t av_bytes(int ndiags) { return (size_t)ndiags * R * sizeof(VT); }
-    __host__ __device__ static size_t stage_bytes(int ndiags, int nruns) {
-        const size_t b = av_bytes(ndiags) + (size_t)nruns * XL * sizeof(T);
-        return (b + 127) / 128 * 128;
-    }
-};
-
-template <typename VT, typename T>
-__device__ __forceinline__ T bulk_value(VT v) {
-    if constexpr (sizeof(VT) == sizeof(T)) return v;
-    else return __uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);   // BF16 -> FP32, exact
-}
-
-template <typename VT, typename T, int NT, int RPT, bool ACC>
-__global__ void __launch_bounds__(NT, 1) spmv_dia_bulk_kernel(
-    int32_t n, int32_t ndiags, int32_t npad, const int32_t* __restrict__ doff, const int2* __restrict__ runs,
-    int32_t nruns, int32_t stages, const VT* __restrict__ av, const T* __restrict__ x, T* __restrict__ y,
-    DotEpilogue ep) {
-    constexpr int R = NT * RPT;
-    using L = BulkLayout<VT, T, R>;
-    constexpr int A = L::A;
-    constexpr int XL = L::XL;
-    static_assert(sizeof(T) == 8 || RPT == 4, "the FP32 path reads 12-float x windows for 4 rows");
-    extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ uint64_t s_full[kBulkMaxStages];
-    __shared__ int32_t s_off[kBulkMaxDiags];
-    __shared__ int32_t s_run0[kBulkMaxRuns], s_rlen[kBulkMaxRuns], s_xlo[kBulkMaxRuns];
-    pdl_wait();
-    pdl_trigger();
-    if (ep.st && ep.st->done) return;   // uniform: CG already finished
-    const int tid = threadIdx.x;
-    for (int k = tid; k < ndiags; k += NT) s_off[k] = doff[k];
-    for (int q = tid; q < nruns; q += NT) {
-        const int2 rq = runs[q];
-        s_run0[q] = rq.x;
-        s_rlen[q] = rq.y;
-        s_xlo[q] = doff[rq.x] & ~(A - 1);   // the run's first offset rounded down to 16 bytes
-    }
-    if (tid == 0) {
-        for (int k = 0; k < stages; ++k) mbar_init(&s_full[k], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    int32_t lo = 0, hi = 0;   // x slices of a strip at i0 span [i0 + lo, i0 + hi)
-    for (int q = 0; q < nruns; ++q) {
-        lo = (q == 0 || s_xlo[q] < lo) ? s_xlo[q] : lo;
-        hi = (q == 0 || s_xlo[q] + XL > hi) ? s_xlo[q] + XL : hi;
-    }
-    const int64_t nA = (int64_t)n & ~(int64_t)(A - 1);   // x copies stay inside the first nA elements
-    auto staged = [&](int64_t i0) { return i0 + R <= n && i0 + lo >= 0 && i0 + hi <= nA; };
-    const size_t avb = L::av_bytes(ndiags);
-    const size_t sb = L::stage_bytes(ndiags, nruns);
-    const uint32_t tx = (uint32_t)(avb + (size_t)nruns * XL * sizeof(T));
-    const int64_t nstrips = ((int64_t)n + R - 1) / R;
-    const int64_t first = blockIdx.x, step = gridDim.x;
-    const int64_t mine = first < nstrips ? (nstrips - 1 - first) / step + 1 : 0;
-
-    // The copies of my k-th strip into its stage, issued by the 32 lanes of warp 0 together
-    // (lane 0 first posts the byte count; one copy per diagonal slice and per run's x slice).
-    auto issue = [&](int64_t k) {
-        uint64_t* bar = &s_full[k % stages];
-        const int64_t i0 = (first + k * step) * R;
-        if (!staged(i0)) {
-            if (tid == 0) mbar_arrive(bar);
-            return;
-        }
-        unsigned char* base = dsm + (size_t)(k % stages) * sb;
-        if (tid == 0) mbar_arrive_expect_tx(bar, tx);
-        __syncwarp();
-        fence_proxy_async_smem();
-        T* xs = reinterpret_cast<T*>(base + avb);
-        for (int c = tid; c < ndiags + nruns; c += 32) {
-            if (c < ndiags)
-                bulk_copy_g2s_stream(base + (size_t)c * R * sizeof(VT), av + (int64_t)c * npad + i0, R * sizeof(VT),
-                                     bar);
-            else
-                bulk_copy_g2s(xs + (size_t)(c - ndiags) * XL, x + i0 + s_xlo[c - ndiags], XL * sizeof(T), bar);
-        }
-    };
-    if (tid < 32)
-        for (int64_t k = 0; k < mine && k < stages; ++k) issue(k);
-
-    T d = T(0);
-    int64_t issued = mine < stages ? mine : stages;
-    int64_t k = 0;
-    for (; k < mine; ++k) {
-        const bool ok = mbar_wait_bounded(&s_full[k % stages], (uint32_t)((k / stages) & 1));
-        if (__syncthreads_or(!ok)) {   // uniform: some thread timed out
-            if (tid == 0) {
-                atomicOr(&g_dia_bulk_fault, 1u);
-                if (ep.st) {   // stop the CG iteration this SpMV belongs to
-                    ep.st->phase = CG_FAULT;
-                    ep.st->done = 1;
-                }
-            }
-            break;
-        }
-        const int64_t i0 = (first + k * step) * R;
-        const int64_t r0 = i0 + (int64_t)tid * RPT;
-        T acc[RPT];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) acc[r] = T(0);
-        if (staged(i0)) {
-            const unsigned char* base = dsm + (size_t)(k % stages) * sb;
-            const VT* avs = reinterpret_cast<const VT*>(base);
-            const T* xs = reinterpret_cast<const T*>(base + avb);
-            for (int q = 0; q < nruns; ++q) {
-                const int j0 = s_run0[q], len = s_rlen[q];
-                const int m = s_off[j0] - s_xlo[q];   // 0 .. A - 1
-                const T* xq = xs + (size_t)q * XL + tid * RPT;
-                if constexpr (sizeof(T) == 8) {
-                    for (int t = 0; t < len; ++t) {
-                        const VT* a = avs + (size_t)(j0 + t) * R + tid * RPT;
-#pragma unroll
-                        for (int r = 0; r < RPT; ++r) acc[r] = fma_t(bulk_value<VT, T>(a[r]), xq[m + t + r], acc[r]);
-                    }
-                } else {
-                    float w[12];
-#pragma unroll
-                    for (int u = 0; u < 3; ++u) {
-                        const float4 t4 = reinterpret_cast<const float4*>(xq)[u];
-                        w[4 * u] = t4.x; w[4 * u + 1] = t4.y; w[4 * u + 2] = t4.z; w[4 * u + 3] = t4.w;
-                    }
-#pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        if (t < len) {
-                            float a[4];
-                            const VT* ap = avs + (size_t)(j0 + t) * R + tid * 4;
-                            if constexpr (sizeof(VT) == 4) {
-                                const float4 v4 = *reinterpret_cast<const float4*>(ap);
-                                a[0] = v4.x; a[1] = v4.y; a[2] = v4.z; a[3] = v4.w;
-                            } else {
-                                const uint2 v2 = *reinterpret_cast<const uint2*>(ap);
-                                a[0] = __uint_as_float(v2.x << 16); a[1] = __uint_as_float(v2.x & 0xffff0000u);
-                                a[2] = __uint_as_float(v2.y << 16); a[3] = __uint_as_float(v2.y & 0xffff0000u);
-                            }
-                            switch (m + t) {   // uniform across the CTA
-                                case 0: dia_f32_fma<0>(a, w, acc); break;
-                                case 1: dia_f32_fma<1>(a, w, acc); break;
-                                case 2: dia_f32_fma<2>(a, w, acc); break;
-                                case 3: dia_f32_fma<3>(a, w, acc); break;
-                                case 4: dia_f32_fma<4>(a, w, acc); break;
-                                default: dia_f32_fma<5>(a, w, acc); break;
-                            }
-                        }
-                    }
-                }
-            }
-        } else {   // a strip at either end: global loads with bounds checks, diagonals in order
-            for (int j = 0; j < ndiags; ++j) {
-                const int32_t off = s_off[j];
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    const int64_t i = r0 + r, kk = i + off;
-                    if (i < n && kk >= 0 && kk < n)
-                        acc[r] = fma_t(bulk_value<VT, T>(av[(int64_t)j * npad + i]), __ldg(x + kk), acc[r]);
-                }
-            }
-        }
-        if constexpr (sizeof(T) == 4 && !ACC) {
-            if (r0 + 4 <= n) {
-                reinterpret_cast<float4*>(y + r0)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                if (ep.st) {
-                    const float4 xv = __ldg(reinterpret_cast<const float4*>(x + r0));
-                    d = fmaf(xv.x, acc[0], d);
-                    d = fmaf(xv.y, acc[1], d);
-                    d = fmaf(xv.z, acc[2], d);
-                    d = fmaf(xv.w, acc[3], d);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < RPT; ++r)
-                    if (r0 + r < n) {
-                        y[r0 + r] = acc[r];
-                        if (ep.st) d = fmaf(__ldg(x + r0 + r), acc[r], d);
-                    }
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                if (r0 + r < n) {
-                    store_y(y, r0 + r, acc[r], ACC);
-                    if (ep.st) d = fma_t(__ldg(x + r0 + r), acc[r], d);
-                }
-            }
-        }
-        __syncthreads();   // every thread is done with this stage
-        if (issued < mine) {
-            if (tid < 32) issue(issued);
-            ++issued;
-        }
-    }
-    if (k < mine && tid == 0) {   // timed out: let the copies in flight land before leaving
-        for (int64_t kk = k; kk < issued; ++kk) (void)mbar_wait_bounded(&s_full[kk % stages], (uint32_t)((kk / stages) & 1));
-    }
-    if (ep.st) finish_dot_nt<T, NT>(d, ep);
 }
 
 // ---------------------------------------------------------------------------
@@ -1488,8 +1205,11 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
     }
 }
 
+// y = 0. Inside CG (st set) a launch after the iteration has stopped does nothing, like the
+// other kernels of the iteration.
 template <typename T>
-__global__ void fill_zero_kernel(T* __restrict__ y, int64_t n) {
+__global__ void fill_zero_kernel(T* __restrict__ y, int64_t n, const CgState* st) {
+    if (st && st->done) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         y[i] = T(0);
@@ -1538,7 +1258,7 @@ mspv_status build_csr_long_rows(mspv_matrix* M, cudaStream_t s) {
     MSPV_TRY(pos.alloc(sizeof(int32_t) * (size_t)M->nrows));
     MSPV_TRY(total.alloc(sizeof(int32_t)));
     unsigned grid = (unsigned)(((int64_t)M->nrows + kThreads - 1) / kThreads);
-    if (grid > (unsigned)kNumSMs * 64) grid = kNumSMs * 64;
+    if (grid > (unsigned)num_sms() * 64) grid = num_sms() * 64;
     csr_long_flag_kernel<<<grid, kThreads, 0, s>>>(M->irp, M->nrows, long_len, flags.as<int32_t>());
     MSPV_CUDA_TRY(cudaGetLastError());
     MSPV_TRY(exclusive_scan_i32(flags.as<int32_t>(), pos.as<int32_t>(), M->nrows, total.as<int32_t>(), s));
@@ -1563,7 +1283,7 @@ mspv_status build_csr_row_blocks(mspv_matrix* M, cudaStream_t s) {
     M->bytes += (M->nblocks + 1) * 4;
     const int64_t threads = (int64_t)M->nrows + 1;
     unsigned grid = (unsigned)((threads + kThreads - 1) / kThreads);
-    if (grid > (unsigned)kNumSMs * 64) grid = kNumSMs * 64;
+    if (grid > (unsigned)num_sms() * 64) grid = num_sms() * 64;
     csr_row_block_kernel<<<grid, kThreads, 0, s>>>(M->irp, M->nrows, M->nblocks, M->row_block);
     MSPV_CUDA_TRY(cudaGetLastError());
     return MSPV_OK;
@@ -1575,7 +1295,7 @@ static inline unsigned blocks_for(int64_t threads) {
 
 static int64_t vector_grid(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)kNumSMs * 8;
+    const int64_t cap = (int64_t)num_sms() * 8;
     if (b > cap) b = cap;
     return b < 1 ? 1 : b;
 }
@@ -1609,76 +1329,12 @@ static int64_t dia_strip_rows(int vt, bool f32) {
 
 static int64_t csr_grid_for(const mspv_matrix* A);
 
-// The bulk-copy DIA kernel's shape per value type and arithmetic: threads per CTA and rows
-// per thread (FP64: one row per thread, 256-row strips; FP32 arithmetic: the 4-row x windows,
-// 512-row strips), and whether it exists for that pair.
-template <typename VT, typename T> struct BulkShape { static constexpr bool ok = false; static constexpr int NT = 1, RPT = 1; };
-template <> struct BulkShape<double, double> { static constexpr bool ok = true; static constexpr int NT = 256, RPT = 1; };
-template <> struct BulkShape<float, float> { static constexpr bool ok = true; static constexpr int NT = 128, RPT = 4; };
-template <> struct BulkShape<__nv_bfloat16, float> { static constexpr bool ok = true; static constexpr int NT = 128, RPT = 4; };
-
-constexpr size_t kBulkSmemBudget = 232448 - 6144;   // 227 KB per CTA, less the static shared memory
-
-struct DiaBulkPlan {
-    bool use = false;
-    int stages = 0;
-    size_t smem = 0;
-    int64_t grid = 0;
-};
-
-// MSPV_DIA_BULK=1 selects the bulk-copy kernel where it applies. It is off by default: on
-// GB300 it measured 2.2x slower than the strip kernel in FP64 (221.9 vs 102.9 us, 128^3
-// stencil) and 4x slower with BF16 values in FP32 arithmetic (127.5 vs 31.4 us). ncu: one
-// CTA per SM (the stages fill shared memory) leaves 8 warps per SM, and their single FMA
-// chains stall on shared-memory latency, the per-strip barrier and FP64 dependencies
-// (FP64 pipe 42 % busy, against 87.5 % for the strip kernel's 64 warps per SM).
-static bool dia_bulk_enabled() {
-    const char* v = std::getenv("MSPV_DIA_BULK");
-    return v && v[0] == '1';
-}
-
-// When the bulk-copy kernel runs for A: at most 32 diagonals in at most 32 runs, a 16-byte
-// aligned AV, at least four strips per SM (smaller matrices keep the many-CTA kernel), and at
-// least two stages in shared memory. The launch also needs x and y 16-byte aligned.
-template <typename VT, typename T>
-static DiaBulkPlan dia_bulk_plan(const mspv_matrix* A) {
-    DiaBulkPlan p;
-    if constexpr (BulkShape<VT, T>::ok) {
-        constexpr int R = BulkShape<VT, T>::NT * BulkShape<VT, T>::RPT;
-        using L = BulkLayout<VT, T, R>;
-        if (!dia_bulk_enabled() || A->ndiags < 1 || A->ndiags > kBulkMaxDiags || A->ndruns < 1 ||
-            A->ndruns > kBulkMaxRuns || reinterpret_cast<uintptr_t>(A->av) % 16 != 0)
-            return p;
-        const int64_t nstrips = ((int64_t)A->nrows + R - 1) / R;
-        if (nstrips < 4 * (int64_t)kNumSMs) return p;
-        const size_t sb = L::stage_bytes(A->ndiags, A->ndruns);
-        const int stages = (int)std::min<size_t>(kBulkMaxStages, kBulkSmemBudget / sb);
-        if (stages < 2) return p;
-        p.use = true;
-        p.stages = stages;
-        p.smem = (size_t)stages * sb;
-        p.grid = std::min<int64_t>(nstrips, kNumSMs);   // one CTA per SM (shared memory)
-    }
-    return p;
-}
-
-static DiaBulkPlan dia_bulk_plan_for(const mspv_matrix* A, bool f32) {
-    switch (A->value_type) {
-        case MSPV_F64: return f32 ? DiaBulkPlan{} : dia_bulk_plan<double, double>(A);
-        case MSPV_F32: return f32 ? dia_bulk_plan<float, float>(A) : DiaBulkPlan{};
-        default: return f32 ? dia_bulk_plan<__nv_bfloat16, float>(A) : DiaBulkPlan{};
-    }
-}
-
 // CTAs of the fused-dot SpMV launch in FP64 or FP32 arithmetic: the number of p.q partials
 // it writes, which the CG's alpha kernel sums. Only DIA launches differ between the two
-// (BF16 values: 8 rows per thread in FP64, 4 in FP32; the bulk-copy kernel one CTA per SM;
-// CG's vectors are 16-byte aligned, so its SpMV takes the bulk kernel whenever the plan does).
+// (BF16 values: 8 rows per thread in FP64, 4 in FP32).
 int64_t spmv_partials_count(const mspv_matrix* A, bool f32) {
     switch (A->format) {
         case MSPV_DIA: {
-            const DiaBulkPlan bp = dia_bulk_plan_for(A, f32);
-            if (bp.use) return bp.grid;
             const int64_t strip = dia_strip_rows(A->value_type, f32);
             const int64_t g = ((int64_t)A->nrows + strip - 1) / strip;
             return g < 1 ? 1 : g;
@@ -1694,29 +1350,8 @@ int64_t spmv_partials_needed(const mspv_matrix* A) {
     return std::max(spmv_partials_count(A, false), spmv_partials_count(A, true));
 }
 
-template <typename VT, typename T, bool ACC>
-static void launch_dia_bulk(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep,
-                            const DiaBulkPlan& bp) {
-    constexpr int NT = BulkShape<VT, T>::NT, RPT = BulkShape<VT, T>::RPT;
-    auto kernel = spmv_dia_bulk_kernel<VT, T, NT, RPT, ACC>;
-    static const bool attr_ok =
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBulkSmemBudget) ==
-        cudaSuccess;
-    (void)attr_ok;   // a refusal surfaces as a launch error
-    launch_kernel(ep.pdl, kernel, (unsigned)bp.grid, NT, bp.smem, s, A->nrows, A->ndiags, A->npad, A->doff,
-                  (const int2*)A->druns, A->ndruns, (int32_t)bp.stages, static_cast<const VT*>(A->av), x, y, ep);
-}
-
 template <typename VT, typename T>
 static void launch_dia(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, DotEpilogue ep) {
-    if constexpr (BulkShape<VT, T>::ok) {
-        const DiaBulkPlan bp = dia_bulk_plan<VT, T>(A);
-        if (bp.use && reinterpret_cast<uintptr_t>(x) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0) {
-            if (ep.acc) launch_dia_bulk<VT, T, true>(A, x, y, s, ep, bp);
-            else launch_dia_bulk<VT, T, false>(A, x, y, s, ep, bp);
-            return;
-        }
-    }
     constexpr int RPT = DiaVec<VT, T>::RPT;
     constexpr int NT = sizeof(T) == 4 ? DiaF32Shape<VT>::NT : kThreads;
     const int64_t strip = (int64_t)NT * RPT;
@@ -1762,7 +1397,7 @@ static int64_t csr_warp_grid(int32_t nrows) {
     }();
     const int64_t groups = ((int64_t)nrows + 31) / 32;
     int64_t g = (groups + kCsrWarpThreads / 32 - 1) / (kCsrWarpThreads / 32);
-    const int64_t wave = (int64_t)kNumSMs * per_sm;
+    const int64_t wave = (int64_t)num_sms() * per_sm;
     if (g > wave) g = wave;
     return g < 1 ? 1 : g;
 }
@@ -1770,11 +1405,11 @@ static int64_t csr_warp_grid(int32_t nrows) {
 // CTAs of the V-lane kernels (a CTA covers kThreads rows for V <= 8, kThreads / V rows for
 // wider rows); with a dot-product epilogue (inside CG) at most two waves of 8 CTAs per SM, the
 // warps striding over the rows.
-constexpr int64_t kCsrCgGridCap = (int64_t)kNumSMs * 8 * 2;
 static int64_t csr_vector_grid(const mspv_matrix* A, bool capped) {
     const int64_t lanes_per_row = A->csr_vector <= 8 ? 1 : A->csr_vector;
     int64_t g = ((int64_t)A->nrows * lanes_per_row + kThreads - 1) / kThreads;
-    if (capped && g > kCsrCgGridCap) g = kCsrCgGridCap;
+    const int64_t cap = (int64_t)num_sms() * 8 * 2;
+    if (capped && g > cap) g = cap;
     return g < 1 ? 1 : g;
 }
 
@@ -1853,9 +1488,11 @@ static void launch_coo(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
     int64_t nch;
     // The chunked kernels write only rows that have entries: rows without any are zeroed here,
     // in parallel, before them (y = A x; for y += A x they stay as they are). The row-block
-    // kernel writes every row of its blocks itself.
-    if (!(A->coo_kernel == 2 && A->coo_rb) && !ep.acc && A->empty_rows > 0)   // a plain launch: waits for
-        fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, (int64_t)A->nrows);   // its predecessor
+    // kernel writes every row of its blocks itself. A plain launch: it waits for its
+    // predecessor.
+    if (!(A->coo_kernel == 2 && A->coo_rb) && !ep.acc && A->empty_rows > 0)
+        fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, (int64_t)A->nrows,
+                                                                                   (const CgState*)ep.st);
     if (A->coo_kernel == 2 && A->coo_rb) {
         const unsigned g = (unsigned)((A->coo_nrb + kThreads / 32 - 1) / (kThreads / 32));
         launch_kernel(ep.pdl, spmv_coo_rb_kernel<VT, T>, g, kThreads, 0, s, A->nrows, A->nnz, A->ai, A->aj,
@@ -1894,13 +1531,13 @@ mspv_status launch_coo_raw(int32_t nrows, int64_t nnz, const int32_t* ai, const 
                            cudaStream_t s) {
     if (nrows == 0) return MSPV_OK;
     if (nnz == 0) {
-        fill_zero_kernel<double><<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows);
+        fill_zero_kernel<double><<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows, nullptr);
         MSPV_CUDA_TRY(cudaGetLastError());
         return MSPV_OK;
     }
     const int64_t nwin = (nnz + kCooWindow - 1) / kCooWindow;
     // rows without entries (unknown for raw triplets) are zeroed first; the kernel writes the others
-    fill_zero_kernel<double><<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows);
+    fill_zero_kernel<double><<<(unsigned)vector_grid(nrows), kThreads, 0, s>>>(y, nrows, nullptr);
     launch_coo_windows<double, double>(nrows, nnz, ai, aj, av, x, y, carry, nwin, s, nullptr);
     MSPV_CUDA_TRY(cudaGetLastError());
     return MSPV_OK;
@@ -1911,7 +1548,7 @@ static mspv_status launch_spmv_t(const mspv_matrix* A, const T* x, T* y, cudaStr
     if (A->nrows == 0) return MSPV_OK;
     if (A->format == MSPV_COO && A->nnz == 0) {
         if (ep.st) return set_error(MSPV_EINVAL, "cg: matrix has no entries");
-        fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, A->nrows);
+        fill_zero_kernel<T><<<(unsigned)vector_grid(A->nrows), kThreads, 0, s>>>(y, A->nrows, nullptr);
         MSPV_CUDA_TRY(cudaGetLastError());
         return MSPV_OK;
     }

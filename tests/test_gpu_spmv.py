@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from _parity import assert_spmv_parity, assert_structure_equal
+from _parity import assert_spmv_parity, assert_structure_equal, spmv_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -413,10 +413,10 @@ def test_fp32_arithmetic_spmv_rejects_bad_input(mspv):
 
 
 # ---------------------------------------------------------------------------
-# the bulk-copy DIA kernel (persistent CTAs, operands staged by bulk asynchronous copies;
-# opt-in with MSPV_DIA_BULK=1, the tests set the switch both ways)
+# DIA with distant and ragged diagonals: a banded matrix whose offsets reach past several
+# 512-row strips, ending in a partial strip
 # ---------------------------------------------------------------------------
-BULK_OFFSETS = [-700, -699, -13, -5, -4, -3, -2, 0, 1, 2, 9, 10, 11, 12, 600, 1201]
+BAND_OFFSETS = [-700, -699, -13, -5, -4, -3, -2, 0, 1, 2, 9, 10, 11, 12, 600, 1201]
 
 
 def _banded_coo(n, offsets, seed):
@@ -434,87 +434,41 @@ def _banded_coo(n, offsets, seed):
     return r, c, v
 
 
-def _bulk_cases(rows_per_strip):
-    """A stencil and a ragged banded matrix with enough strips for the bulk path (four per SM)."""
-    g = 64 if rows_per_strip == 256 else 96
-    n_band = 152 * 4 * rows_per_strip + (37 if rows_per_strip == 256 else 3)
-    return [("stencil%d" % g, g ** 3, lambda: synth.stencil27(g)),
-            ("banded_ragged", n_band, lambda: _banded_coo(n_band, BULK_OFFSETS, 5))]
-
-
-@pytest.mark.parametrize("which", [0, 1], ids=["stencil", "banded_ragged"])
-def test_dia_bulk_kernel_fp64(mspv, orc, monkeypatch, which):
-    """FP64 DIA through the bulk-copy kernel against the one-CTA-per-strip kernel, bit for bit
-    (each row's FMAs run over the diagonals in storage order in both), for y = A x and
-    y += A x, and against the oracle; the first and last strips take the bounds-checked path
-    and the banded matrix ends in a partial strip."""
-    name, n, gen = _bulk_cases(256)[which]
-    r, c, v = gen()
+def test_dia_banded_ragged_fp64(mspv, orc):
+    """FP64 DIA on 16 diagonals between -700 and +1201 over 155,685 rows (the last strip
+    partial), y = A x and y += A x, against the oracle's Algorithm 3."""
+    n = 152 * 4 * 256 + 37
+    r, c, v = _banded_coo(n, BAND_OFFSETS, 5)
     A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
     D = A.convert("dia")
     O = orc.coo_to_dia(orc.canonicalize(n, n, r, c, v))
     x = synth.uniform_x(n, 9) * 2 - 1
     xd = dev(x)
-    y0 = dev(synth.uniform_x(n, 10))
-    out = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("MSPV_DIA_BULK", flag)
-        ya = y0.clone()
-        D.spmv_add(xd, ya)
-        out[flag] = (D.spmv(xd).cpu().numpy(), ya.cpu().numpy())
-    assert np.array_equal(out["1"][0], out["0"][0])
-    assert np.array_equal(out["1"][1], out["0"][1])
-    assert_spmv_parity(out["1"][0], O, x, orc)
-    mspv.device_status()
+    y0 = synth.uniform_x(n, 10)
+    ya = dev(y0)
+    D.spmv_add(xd, ya)
+    assert_spmv_parity(D.spmv(xd).cpu().numpy(), O, x, orc)
+    # y += A x: one more rounding of the sum
+    want = y0 + orc.spmv(O, x)
+    bound = spmv_tolerance(O, x, orc) + 2.0 ** -52 * np.abs(want)
+    assert np.all(np.abs(ya.cpu().numpy() - want) <= bound)
 
 
 @pytest.mark.parametrize("vt", ["f32", "bf16"])
-@pytest.mark.parametrize("which", [0, 1], ids=["stencil", "banded_ragged"])
-def test_dia_bulk_kernel_fp32_arithmetic(mspv, orc, monkeypatch, vt, which):
-    """FP32-arithmetic DIA (FP32 / BF16 values) through the bulk-copy kernel: bit for bit the
-    one-CTA-per-strip kernel's result (same x windows, same FMA order), and within the FP32
-    bound of the oracle."""
-    name, n, gen = _bulk_cases(512)[which]
-    r, c, v = gen()
+def test_dia_banded_ragged_fp32_arithmetic(mspv, orc, vt):
+    """FP32-arithmetic DIA (FP32 / BF16 values) on the banded matrix: within the FP32 bound
+    2 (k + 2) 2^-24 sum |a x| of the oracle's product on the rounded values."""
+    n = 152 * 4 * 512 + 3
+    r, c, v = _banded_coo(n, BAND_OFFSETS, 5)
     A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
     D = A.convert("dia", vt)
     O = orc.with_values(orc.coo_to_dia(orc.canonicalize(n, n, r, c, v)), vt)
     x32 = (synth.uniform_x(n, 11) * 2 - 1).astype(np.float32)
-    xd = dev(x32)
-    out = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("MSPV_DIA_BULK", flag)
-        out[flag] = D.spmv_f32(xd).cpu().numpy()
-    assert np.array_equal(out["1"], out["0"])
+    got = D.spmv_f32(dev(x32)).cpu().numpy()
     x64 = x32.astype(np.float64)
     want = orc.spmv(O, x64)
     absO = orc.Matrix(O.fmt, O.nrows, O.ncols, O.nnz, ai=O.ai, aj=O.aj, irp=O.irp, av=np.abs(O.av),
                       doff=O.doff, npad=O.npad)
     scale = orc.spmv(absO, np.abs(x64))
     bound = 2.0 * (O.ndiags + 2) * 2.0 ** -24 * scale + 1e-30
-    assert np.all(np.abs(out["1"].astype(np.float64) - want) <= bound)
-    mspv.device_status()
-
-
-def test_dia_bulk_kernel_in_cg(mspv, orc, monkeypatch):
-    """FP64 CG on the 64^3 stencil with the bulk-copy SpMV (one p.q partial per CTA) and with
-    the strip kernel: same iteration count to 1e-10, iterates equal to rounding, and 30 fixed
-    iterations track the oracle's."""
-    g = 64
-    n = g ** 3
-    r, c, v = synth.stencil27(g)
-    A = mspv.Matrix.from_coo(n, n, dev(r), dev(c), dev(v))
-    D = A.convert("dia")
-    O = orc.coo_to_dia(orc.canonicalize(n, n, r, c, v))
-    b = orc.spmv(O, synth.uniform_x(n, 12))
-    res = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("MSPV_DIA_BULK", flag)
-        res[flag] = D.cg(dev(b), tol=1e-10, maxit=2000)
-    assert res["1"].converged and res["1"].iters == res["0"].iters
-    x1, x0 = res["1"].x.cpu().numpy(), res["0"].x.cpu().numpy()
-    assert np.max(np.abs(x1 - x0)) <= 1e-9 * np.max(np.abs(x0))
-    monkeypatch.setenv("MSPV_DIA_BULK", "1")
-    r30 = D.cg(dev(b), tol=0.0, maxit=30)
-    xo, _, _, _, _, _ = orc.cg(O, b, tol=0.0, maxit=30)
-    assert np.max(np.abs(r30.x.cpu().numpy() - xo)) <= 1e-11 * np.max(np.abs(xo))
+    assert np.all(np.abs(got.astype(np.float64) - want) <= bound)

@@ -1,5 +1,6 @@
 """The allocation-free COO SpMV entry point (mspv_spmv_coo_noalloc), called through the
-C ABI, against the regular entry point (create_coo + spmv) on the same matrix.
+C ABI, against the regular entry point (create_coo + spmv) on the same matrix and against
+the CPU oracle's Algorithm 1.
 
 It serves callers that cannot allocate device memory (their memory is reserved or
 budgeted by their own allocator); its scratch is a fixed array inside the library, so
@@ -9,6 +10,7 @@ import numpy as np
 import pytest
 
 import synth
+from _parity import assert_spmv_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +69,64 @@ def test_noalloc_matches_regular_entry_point_twice(mspv):
         bound = _bound(mspv, n, e, x)
         err = np.abs(got - want)
         assert np.all(err <= bound), f"call {call}: max excess {np.max(err - bound):.3e}"
+
+
+def _oracle_check(orc, n, rows, cols, vals, x, got):
+    """The oracle's Algorithm 1 on the same triplets, at the single-result parity bound
+    max(1e-13, 2 (k + 2) u) * sum_j |a_ij x_j| of the other SpMV tests."""
+    O = orc.Matrix(orc.COO, n, n, rows.size, ai=rows.astype(np.int32), aj=cols.astype(np.int32),
+                   av=vals.astype(np.float64))
+    assert_spmv_parity(got, O, x, orc)
+
+
+def test_noalloc_matches_oracle_twice(mspv, orc):
+    """Row-sorted triplets with duplicates and empty rows, checked against the CPU oracle
+    directly on two calls in a row (the second sees the first call's scratch)."""
+    n, r, c, v = _matrix(23)
+    order = np.argsort(r, kind="stable")            # rows non-decreasing, columns in input order
+    r, c, v = r[order], c[order], v[order]
+    dev = torch.device("cuda")
+    rows, cols, vals = (torch.from_numpy(a).to(dev) for a in (r, c, v))
+    for seed in (3, 4):
+        xh = synth.uniform_x(n, seed) * 2 - 1
+        y = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+        mspv.spmv_coo_noalloc(n, n, rows, cols, vals, torch.from_numpy(xh).to(dev), y)
+        _oracle_check(orc, n, r, c, v, xh, y.cpu().numpy())
+
+
+def test_noalloc_row_spanning_whole_windows(mspv, orc):
+    """One row of 4 x 3072 + 100 entries starting exactly on a window boundary (entry 3072):
+    its sum runs through the fix-up chain over three whole middle windows."""
+    w = 3072
+    rng = np.random.default_rng(31)
+    n = 5000
+    head_rows = np.sort(rng.integers(0, 1000, w)).astype(np.int32)      # exactly one window
+    long_rows = np.full(4 * w + 100, 1500, np.int32)
+    tail_rows = np.sort(rng.integers(1501, n, 7000)).astype(np.int32)
+    r = np.concatenate([head_rows, long_rows, tail_rows])
+    c = rng.integers(0, n, r.size).astype(np.int32)
+    v = rng.uniform(-1, 1, r.size)
+    assert np.all(np.diff(r) >= 0) and r[w] == 1500 and r[w - 1] < 1500
+    dev = torch.device("cuda")
+    rows, cols, vals = (torch.from_numpy(a).to(dev) for a in (r, c, v))
+    for seed in (5, 6):
+        xh = synth.uniform_x(n, seed) * 2 - 1
+        y = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+        mspv.spmv_coo_noalloc(n, n, rows, cols, vals, torch.from_numpy(xh).to(dev), y)
+        _oracle_check(orc, n, r, c, v, xh, y.cpu().numpy())
+
+
+def test_noalloc_no_entries_zeroes_y(mspv):
+    """nnz = 0 with rows: y = 0 on every row (y starts as NaN)."""
+    dev = torch.device("cuda")
+    n = 777
+    empty_i = torch.zeros(0, dtype=torch.int32, device=dev)
+    empty_v = torch.zeros(0, dtype=torch.float64, device=dev)
+    x = torch.ones(n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        y = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+        mspv.spmv_coo_noalloc(n, n, empty_i, empty_i, empty_v, x, y)
+        assert torch.all(y == 0).item()
 
 
 def test_noalloc_rejects_bad_input(mspv):
