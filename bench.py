@@ -39,15 +39,16 @@ CG_ITERS = 50
 NDIAGS = 27
 # FP64 ALU roofline: 2 FP64 FMA per clock per SM (GB300), 152 SMs, 2070 MHz max SM clock,
 # 2 flops per FMA -> 1.2586 TFLOP/s (NVIDIA's nominal FP64 figure for the part is 1.25).
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+FP64_FMA_PER_CLK_SM = 2
+FP64_PEAK_TFLOPS = 2 * FP64_FMA_PER_CLK_SM * 152 * 2.070e9 / 1e12
 
 
 # DRAM traffic of one spmv_dia_kernel<double, double, false> launch without the CG epilogue,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 96^3 stencil; it is
-# scaled to the bench grid by rows (every stream of the kernel grows with n). Reported only while
-# the source of that launch (the FP64 value loader, the kernel and the FP64 branch of its
-# launcher) is the one that was captured.
-DIA_TRAFFIC = {"bytes": 201_895_424, "rows": 96 ** 3,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch, the first DIA
+# SpMV of the run) on the 128^3 stencil, the benchmark's own grid; other grids scale it by rows
+# (every stream of the kernel grows with n). Reported only while the source of that launch (the
+# FP64 value loader, the kernel and the FP64 branch of its launcher) is the one captured.
+DIA_TRAFFIC = {"bytes": 469_803_264 + 4_328_448, "rows": 128 ** 3,
                "src_sha256": "a4c7fd0698f8ce4ff5159215953bb280fe3cb8407e0ef26678feeca0fd806dec"}
 
 
@@ -184,6 +185,65 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def time_to_solution(mspv, torch, dev, g, perturb_seed, inner_tol):
+    """Time to a 1e-10 relative residual from x0 = 0 on the g^3 stencil, DIA: FP64 CG against
+    FP64-outer mixed precision. Exact values 26 / -1 with b = A 1 (HPCG's right-hand side), or
+    the perturbed SPD stencil, whose values FP32 / BF16 do round, with b = A x* for
+    x* ~ U[0.5, 1.5) (seed 1): its rows sum to 1, so A 1 = 1 is an eigenvector and b = A 1 would
+    converge in one iteration. Each solver runs once untimed, then once timed with CUDA events;
+    max |x - x*| is the error against the exact solution."""
+    n = g ** 3
+    r, c, v = synth.stencil27_torch(g, dev, perturb_seed=perturb_seed)
+    A = mspv.Matrix.from_coo(n, n, r, c, v)
+    del r, c, v
+    D = A.convert("dia")
+    D32 = A.convert("dia", "f32")
+    D16 = A.convert("dia", "bf16")
+    A.close()
+    if perturb_seed is None:
+        xstar = torch.ones(n, dtype=torch.float64, device=dev)
+    else:
+        xstar = torch.from_numpy(synth.uniform_x(n, 1) + 0.5).to(dev)
+    b = D.spmv(xstar)
+    stream = torch.cuda.current_stream()
+    modes = (
+        ("fp64_cg", lambda xx: D.cg(b, x=xx, tol=1e-10, maxit=20000)),
+        # FP32 values with FP64 arithmetic in the inner CG and its SpMV (FP64 accumulation)
+        ("ir_f32_values_fp64_arith", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=1e-5,
+                                                        max_outer=40, maxit_inner=20000)),
+        # FP32 / BF16 values, restarted refinement around an FP32-arithmetic inner CG
+        ("ir_f32_values_fp32_inner", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=inner_tol,
+                                                        max_outer=40, maxit_inner=20000, inner_fp32=True)),
+        ("ir_bf16_values_fp32_inner", lambda xx: D.cg_ir(D16, b, x=xx, tol=1e-10, inner_tol=inner_tol,
+                                                         max_outer=40, maxit_inner=20000, inner_fp32=True)),
+        # one FP32-arithmetic CG with reliable FP64 residual updates
+        ("ru_f32_values", lambda xx: D.cg_ru(D32, b, x=xx, tol=1e-10, max_updates=400, maxit=20000)),
+        ("ru_bf16_values", lambda xx: D.cg_ru(D16, b, x=xx, tol=1e-10, max_updates=400, maxit=20000)),
+    )
+    os.environ["MSPV_CG_CHECK_EVERY"] = "10"
+    out = {}
+    for label, fn in modes:
+        xx = torch.zeros(n, dtype=torch.float64, device=dev)
+        fn(xx)
+        xx.zero_()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        res = fn(xx)
+        e0.record(stream)
+        torch.cuda.synchronize()
+        out[label] = {"ms": round(s0.elapsed_time(e0), 3), "iters": res.iters, "outer": res.outer_iters,
+                      "relres": res.relres, "converged": res.converged,
+                      "max_abs_err": float((xx - xstar).abs().max().item())}
+    base = out["fp64_cg"]["ms"]
+    for label, rec in out.items():
+        rec["speedup_vs_fp64_cg"] = round(base / rec["ms"], 3)
+    for M in (D, D32, D16):
+        M.close()
+    return out
+
+
 def run_mspv(args, world, rank, local):
     import torch
     import paper_2304_09511_gb300 as mspv
@@ -390,6 +450,19 @@ def run_mspv(args, world, rank, local):
         tt[label] = {"ms": round(s3.elapsed_time(e3), 3), "iters": res.iters, "outer": res.outer_iters,
                      "relres": res.relres, "converged": res.converged}
 
+    # time to solution on the larger stencil, exact and perturbed values
+    tts = {}
+    if args.tts_grid > 0:
+        tts["exact"] = time_to_solution(mspv, torch, dev, args.tts_grid, None, args.ir_inner_tol)
+        tts["perturbed"] = time_to_solution(mspv, torch, dev, args.tts_grid, 3, args.ir_inner_tol)
+
+    # the FP64 FMA rate of this GPU: the peak of the FP64 (ALU-bound) roofline
+    fp64_peak = mspv.fp64_fma_rate()
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(clk["sm_max_mhz"]) if clk and clk.get("sm_max_mhz") else 2070.0
+    derived_peak = 2.0 * FP64_FMA_PER_CLK_SM * sms * sm_mhz * 1e6 / 1e12
+
     dia_launch_ms = ms["dia"]
     dia_s = dia_launch_ms * 1e-3
     achieved_tf = 2.0 * nnz / dia_s / 1e12          # algorithmic flops (2 per stored nonzero)
@@ -407,15 +480,22 @@ def run_mspv(args, world, rank, local):
         "per_format": per_format,
         "cg": {"ms_per_iter": round(cg_ms_iter, 5),
                "GB_s": round(bm["cg_iter"] / (cg_ms_iter * 1e-3) / 1e9, 1),
-               "time_to_1e-10": tt},
+               "time_to_1e-10": tt,
+               f"time_to_1e-10_{args.tts_grid}^3": tts},
         "convert_s": {"coo_sort_coalesce": round(t_coo, 4), "csr": round(t_csr, 4), "dia": round(t_dia, 4)},
         "roofline": {"kernel": "spmv_dia_kernel<double>", "bound": "alu",
-                     "achieved": round(achieved_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                     "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
-                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz x 2 flop",
-                     "executed_fma_frac": round(executed_tf / FP64_PEAK_TFLOPS, 4),
+                     "achieved": round(achieved_tf, 4), "peak": round(derived_peak, 4), "unit": "TFLOP/s",
+                     "frac": round(achieved_tf / derived_peak, 4),
+                     "peak_source": f"derived: {FP64_FMA_PER_CLK_SM} FP64 FMA/clk/SM x {sms} SMs x "
+                                    f"{sm_mhz:.0f} MHz (max SM clock, sampled under load) x 2 flop",
+                     "executed_fma_frac": round(executed_tf / derived_peak, 4),
+                     "fp64_fma_ceiling_measured": round(fp64_peak, 4),
+                     "frac_of_measured_ceiling": round(achieved_tf / fp64_peak, 4),
+                     "ceiling_source": "mspv_fp64_fma_rate on this GPU: one full wave of independent "
+                                       "FP64 FMA chains (4, 8 or 16 per thread), fastest launch",
                      "traffic": dia_traffic(n),
-                     "traffic_source": "ncu dram bytes of one launch on the 96^3 stencil, scaled by rows",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                       "on the 128^3 stencil (scaled by rows at other grids)",
                      "flops_per_launch": 2 * nnz, "bytes_per_launch": bm["dia"],
                      "hbm": {"achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]}},
@@ -809,16 +889,31 @@ def oracle_sample(oracle, n, mats, cg_iters):
 
 
 def cpu_baseline(g, cg_iters):
+    """The oracle timed on this host's cores: the parity build on one core, and its OpenMP
+    timing copy (-O3; CSR / DIA SpMV rows and CG's vector loops across all cores, COO SpMV
+    serial) on every core. The headline value is the all-cores leg."""
     oracle, n, mats = oracle_workload(g)
     nnz = mats["coo"].nnz
     bm = byte_model(n, nnz, mats["dia"].ndiags)
-    t = oracle_sample(oracle, n, mats, cg_iters)
     byts = bm["coo"] + bm["csr"] + bm["dia"] + bm["cg_iter"] * cg_iters + bm["dia"] + 32 * n
-    secs = sum(t.values())
-    return {"value": round(byts / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{g}^3 stencil: one SpMV per format + {cg_iters} CG iterations (DIA), serial C oracle",
-            "seconds": round(secs, 3),
-            "per_format_GB_s": {f: round(bm[f] / t[f] / 1e9, 3) for f in ("coo", "csr", "dia")}}
+    sample = f"{g}^3 stencil: one SpMV per format + {cg_iters} CG iterations (DIA)"
+
+    def leg(t, cores, build):
+        secs = sum(t.values())
+        return {"value": round(byts / secs / 1e9, 3), "unit": "GB/s", "cores": cores, "build": build,
+                "seconds": round(secs, 3),
+                "per_format_GB_s": {f: round(bm[f] / t[f] / 1e9, 3) for f in ("coo", "csr", "dia")},
+                "cg_ms_per_iter": round(t["cg"] / cg_iters * 1e3, 3)}
+
+    serial = leg(oracle_sample(oracle, n, mats, cg_iters), 1, "parity build: gcc -O2, serial C")
+    with oracle.timing_build():
+        cores = oracle.threads()
+        oracle_sample(oracle, n, mats, 2)   # start the thread team
+        all_cores = leg(oracle_sample(oracle, n, mats, cg_iters), cores,
+                        "timing copy: gcc -O3 -fopenmp, no -march (one build for x86-64 and AArch64)")
+    return {"value": all_cores["value"], "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": sample + f"; all-cores leg ({cores} threads) is the value, serial leg beside it",
+            "serial": serial, "all_cores": all_cores}
 
 
 def run_reference(args, world, rank):
@@ -864,6 +959,9 @@ def main():
     ap.add_argument("--ref-cg-iters", type=int, default=1,
                     help="CG iterations per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tts-grid", type=int, default=192,
+                    help="step mode: stencil grid of the time-to-1e-10 block, exact and perturbed "
+                         "values (0 skips it)")
     ap.add_argument("--mode", choices=["step", "selector", "mixed", "split"], default="step",
                     help="step: the SpMV + CG step (default); selector: tuner labels, MLP "
                          "training and held-out regret, then the stencil end to end; mixed: FP64 "

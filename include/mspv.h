@@ -336,6 +336,19 @@ MSPV_API const char* mspv_status_string(mspv_status s);
  */
 MSPV_API int32_t mspv_csr_vector_width(double row_mean, double row_std, int32_t row_max);
 
+/*
+ * FP64 fused multiply-add rate of the current device, in TFLOP/s (2 flops per FMA); device
+ * characterisation, not part of the paper's method. On GB300 the FP64 pipe bounds the FP64
+ * DIA SpMV, whose roofline takes this rate as its peak. One full wave of CTAs (as many as the
+ * device holds at once) runs 4, 8 or 16 independent FMA chains per thread, each a running
+ * sum acc = m * y + acc like an SpMV row (8 chains for `iters`
+ * steps, the same FMA count for the others); for each, one warm-up launch, then the fastest of
+ * `repeats` launches timed with CUDA events on `stream`; the fastest configuration is the rate.
+ * Synchronous; allocates and frees a small device buffer. EINVAL for iters outside
+ * [1, 2^30], repeats < 1 or tflops NULL.
+ */
+MSPV_API mspv_status mspv_fp64_fma_rate(int64_t iters, int32_t repeats, void* stream, double* tflops);
+
 /* Library version, as MAJOR * 10000 + MINOR * 100 + PATCH. */
 MSPV_API int32_t mspv_version(void);
 

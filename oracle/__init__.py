@@ -53,6 +53,44 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build_timing(force: bool = False) -> str:
+    """Compile the CPU-baseline timing copy, liboracle_omp.so: the same source with -O3 and
+    OpenMP (row loops of the CSR / DIA SpMV and CG's vector loops on all host cores, dot
+    products as reductions). Not used for parity. No -march flag: the library builds the
+    same on x86-64 and AArch64 hosts."""
+    stale = (not os.path.exists(_LIB_OMP)
+             or os.path.getmtime(_LIB_OMP) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB_OMP + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                        "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+class timing_build:
+    """Context manager: the oracle functions run on the OpenMP timing copy inside it."""
+
+    def __enter__(self):
+        global _lib
+        self._saved = _lib
+        _lib = _configure(ctypes.CDLL(build_timing()))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def threads() -> int:
+    """Threads the loaded oracle library uses (1 for the parity build)."""
+    return int(_L().orc_threads())
+
+
 class _Mat(ctypes.Structure):
     _fields_ = [("fmt", ctypes.c_int32), ("nrows", ctypes.c_int32), ("ncols", ctypes.c_int32),
                 ("nnz", ctypes.c_int64), ("ai", ctypes.c_void_p), ("aj", ctypes.c_void_p),
@@ -66,28 +104,33 @@ _lib = None
 def _L():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        i32, i64, dbl, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
-        sig = {
-            "orc_coo_canonicalize": (i64, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
-            "orc_coo_to_csr": (None, [i32, i64, vp, vp]),
-            "orc_csr_to_coo": (None, [i32, vp, vp]),
-            "orc_dia_offsets": (i32, [i32, i64, vp, vp, vp]),
-            "orc_coo_to_dia": (None, [i32, i64, vp, vp, vp, i32, vp, i32, vp]),
-            "orc_dia_to_coo": (i64, [i32, i32, vp, i32, vp, vp, vp, vp]),
-            "orc_spmv_coo": (None, [i32, i64, vp, vp, vp, vp, vp]),
-            "orc_spmv_csr": (None, [i32, vp, vp, vp, vp, vp]),
-            "orc_spmv_dia": (None, [i32, i32, vp, i32, vp, vp, vp]),
-            "orc_round_values": (None, [i64, vp, i32, vp]),
-            "orc_cg": (i32, [vp, vp, vp, dbl, i32, vp, vp, vp, vp, vp]),
-            "orc_cg_ir": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, vp, vp]),
-            "orc_cg_ru": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, vp, vp]),
-        }
-        for name, (res, args) in sig.items():
-            fn = getattr(_lib, name)
-            fn.restype = res
-            fn.argtypes = args
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    i32, i64, dbl, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "orc_coo_canonicalize": (i64, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
+        "orc_coo_to_csr": (None, [i32, i64, vp, vp]),
+        "orc_csr_to_coo": (None, [i32, vp, vp]),
+        "orc_dia_offsets": (i32, [i32, i64, vp, vp, vp]),
+        "orc_coo_to_dia": (None, [i32, i64, vp, vp, vp, i32, vp, i32, vp]),
+        "orc_dia_to_coo": (i64, [i32, i32, vp, i32, vp, vp, vp, vp]),
+        "orc_spmv_coo": (None, [i32, i64, vp, vp, vp, vp, vp]),
+        "orc_spmv_csr": (None, [i32, vp, vp, vp, vp, vp]),
+        "orc_spmv_dia": (None, [i32, i32, vp, i32, vp, vp, vp]),
+        "orc_round_values": (None, [i64, vp, i32, vp]),
+        "orc_cg": (i32, [vp, vp, vp, dbl, i32, vp, vp, vp, vp, vp]),
+        "orc_cg_ir": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, vp, vp]),
+        "orc_cg_ru": (i32, [vp, vp, vp, vp, dbl, dbl, i32, i32, vp, vp, vp]),
+        "orc_threads": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
 
 
 def _p(a: np.ndarray | None):

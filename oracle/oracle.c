@@ -33,9 +33,9 @@
  *                         paper's HPCG validation runs with the preconditioner
  *                         disabled (Sec. VI, HPCG experiments), textbook form.
  *   orc_cg_ir             FP64 iterative refinement around an inner CG on the
- *                         low-precision matrix. Not in the paper: parity
- *                         unpinned against the paper, pinned by its final FP64
- *                         residual only.
+ *                         low-precision matrix. Not in the paper: pinned step by
+ *                         step by the dense stationary recursion
+ *                         x += Alo^-1 (b - A64 x) and by its final FP64 residual.
  *   orc_cg_ru             one CG on the low-precision matrix whose residual is
  *                         replaced by the true FP64 residual b - A64 x at
  *                         "reliable updates" (Sleijpen and van der Vorst). Not in
@@ -49,6 +49,28 @@
 #include <string.h>
 
 #include "oracle.h"
+
+/* The CPU-baseline timing copy of this file is compiled with OpenMP: the row loops of the
+ * CSR and DIA SpMV and the vector loops of orc_cg then run on all host cores, and dot
+ * products become reductions (so their rounding order changes there). The parity build
+ * has no OpenMP and these markers expand to nothing. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_ROWS_PARALLEL _Pragma("omp parallel for schedule(static)")
+#define ORC_SUM_PARALLEL _Pragma("omp parallel for schedule(static) reduction(+:s)")   /* sums into s */
+#else
+#define ORC_ROWS_PARALLEL
+#define ORC_SUM_PARALLEL
+#endif
+
+/* Threads the timing copy uses (1 in the parity build). */
+int32_t orc_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* COO canonicalisation: stable merge sort on (row, col), then coalesce.      */
@@ -197,6 +219,7 @@ void orc_spmv_coo(int32_t nrows, int64_t nnz, const int32_t* ai, const int32_t* 
 
 void orc_spmv_csr(int32_t nrows, const int32_t* irp, const int32_t* aj, const double* av,
                   const double* x, double* y) {
+    ORC_ROWS_PARALLEL
     for (int32_t i = 0; i < nrows; i++) {
         double sum = 0.0;
         for (int32_t j = irp[i]; j < irp[i + 1]; j++) sum += av[j] * x[aj[j]];
@@ -206,6 +229,7 @@ void orc_spmv_csr(int32_t nrows, const int32_t* irp, const int32_t* aj, const do
 
 void orc_spmv_dia(int32_t n, int32_t ndiags, const int32_t* doff, int32_t npad,
                   const double* av, const double* x, double* y) {
+    ORC_ROWS_PARALLEL
     for (int32_t i = 0; i < n; i++) {
         double sum = 0.0;
         for (int32_t j = 0; j < ndiags; j++) {
@@ -255,6 +279,7 @@ static void matvec(const orc_matrix* A, const double* x, double* y) {
 
 static double dot(int32_t n, const double* u, const double* v) {
     double s = 0.0;
+    ORC_SUM_PARALLEL
     for (int32_t i = 0; i < n; i++) s += u[i] * v[i];
     return s;
 }
@@ -295,6 +320,7 @@ int32_t orc_cg(const orc_matrix* A, const double* b, double* x, double tol, int3
         goto done;
     }
     matvec(A, x, q);
+    ORC_ROWS_PARALLEL
     for (int32_t i = 0; i < n; i++) { r[i] = b[i] - q[i]; p[i] = r[i]; }
     double rho = dot(n, r, r);
     if (res_hist) res_hist[0] = sqrt(rho) / bnorm;
@@ -306,7 +332,9 @@ int32_t orc_cg(const orc_matrix* A, const double* b, double* x, double tol, int3
         double pq = dot(n, p, q);
         double alpha = rho / pq;
         if (!(pq > 0.0) || !isfinite(alpha)) { status = ORC_BREAKDOWN; break; }
+        ORC_ROWS_PARALLEL
         for (int32_t i = 0; i < n; i++) x[i] = x[i] + alpha * p[i];
+        ORC_ROWS_PARALLEL
         for (int32_t i = 0; i < n; i++) r[i] = r[i] - alpha * q[i];
         double rho_new = dot(n, r, r);
         k++;
@@ -315,6 +343,7 @@ int32_t orc_cg(const orc_matrix* A, const double* b, double* x, double tol, int3
         if (sqrt(rho_new) <= tol * bnorm) { rho = rho_new; converged = 1; break; }
         double beta = rho_new / rho;
         rho = rho_new;
+        ORC_ROWS_PARALLEL
         for (int32_t i = 0; i < n; i++) p[i] = r[i] + beta * p[i];
     }
     *iters = k;

@@ -51,6 +51,7 @@ int32_t orc_cg(const orc_matrix* A, const double* b, double* x, double tol, int3
 int32_t orc_cg_ir(const orc_matrix* A64, const orc_matrix* Alo, const double* b, double* x,
                   double tol, double inner_tol, int32_t max_outer, int32_t maxit_inner,
                   int32_t* outer_iters, int32_t* inner_iters_total, double* relres);
+int32_t orc_threads(void);
 int32_t orc_cg_ru(const orc_matrix* A64, const orc_matrix* Alo, const double* b, double* x,
                   double tol, double delta, int32_t max_updates, int32_t maxit,
                   int32_t* updates, int32_t* iters, double* relres);

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import MspvError, FORMATS, VALUE_TYPES, load
 
-__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "stream_handle",
+__all__ = ["Matrix", "CgResult", "MspvError", "load", "csr_vector_width", "fp64_fma_rate", "stream_handle",
            "spmv_coo_noalloc", "selector_train", "selector_predict", "NUM_FEATURES",
            "SELECTOR_PARAMS"]
 
@@ -61,6 +61,13 @@ def spmv_coo_noalloc(nrows: int, ncols: int, rows, cols, vals, x, y, stream=None
                                             cols.data_ptr(), vals.data_ptr(), x.data_ptr(),
                                             y.data_ptr(), stream_handle(stream)))
     return y
+
+
+def fp64_fma_rate(iters: int = 4096, repeats: int = 3, stream=None) -> float:
+    """FP64 FMA rate of the current device in TFLOP/s (the FP64 roofline's peak)."""
+    out = ctypes.c_double(0.0)
+    _lib.check(load().mspv_fp64_fma_rate(int(iters), int(repeats), stream_handle(stream), ctypes.byref(out)))
+    return out.value
 
 
 def csr_vector_width(row_mean: float, row_std: float = 0.0, row_max: int = 0) -> int:

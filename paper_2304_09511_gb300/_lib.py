@@ -61,6 +61,7 @@ SIGNATURES = {
     "mspv_selector_train": (i32, [vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]),
     "mspv_selector_predict": (i32, [vp, vp, i32, vp, vp]),
     "mspv_select_format": (i32, [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
+    "mspv_fp64_fma_rate": (i32, [i64, i32, vp, ctypes.POINTER(dbl)]),
 }
 
 NUM_FEATURES = 10

@@ -81,10 +81,13 @@ def stencil27(g: int, perturb_seed: int | None = None, planes_per_chunk: int = 1
             u = _unit(_splitmix64(key))
             off = -(1.0 + 0.1 * u)
             v = np.where(rr == cc, 0.0, off)
-            # diagonal = sum |off| + 1, accumulated per row in column order
+            # diagonal = sum |off| + 1, accumulated per row left to right in column order
             Vm = np.zeros((m, 27))
             Vm[valid] = v
-            diag = np.abs(Vm).sum(axis=1) + 1.0
+            diag = np.zeros(m)
+            for k in range(27):
+                diag = diag + np.abs(Vm[:, k])
+            diag = diag + 1.0
             diag_rep = np.broadcast_to(diag[:, None], (m, 27))[valid]
             vals[pos:pos + cnt] = np.where(rr == cc, diag_rep, v)
         pos += cnt
@@ -92,9 +95,26 @@ def stencil27(g: int, perturb_seed: int | None = None, planes_per_chunk: int = 1
     return rows, cols, vals
 
 
-def stencil27_torch(g: int, device, planes_per_chunk: int = 32):
-    """The unperturbed 27-point stencil of stencil27, built by torch on `device` (same
-    triplets, same (row, col) order): for grids whose host generation would be slow."""
+def _as_i64(c: int) -> int:
+    """The int64 with the bit pattern of the uint64 c."""
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _splitmix64_torch(z):
+    """_splitmix64 on int64 tensors holding uint64 bit patterns (products wrap mod 2^64;
+    right shifts are made logical by masking the sign extension)."""
+    def lsr(t, k):
+        return (t >> k) & ((1 << (64 - k)) - 1)
+    z = z + _as_i64(0x9E3779B97F4A7C15)
+    z = (z ^ lsr(z, 30)) * _as_i64(0xBF58476D1CE4E5B9)
+    z = (z ^ lsr(z, 27)) * _as_i64(0x94D049BB133111EB)
+    return z ^ lsr(z, 31)
+
+
+def stencil27_torch(g: int, device, planes_per_chunk: int = 32, perturb_seed: int | None = None):
+    """The 27-point stencil of stencil27 (plain or perturbed), built by torch on `device`:
+    the same triplets bit for bit, in the same (row, col) order, for grids whose host
+    generation would be slow."""
     import torch
     n = g * g * g
     nnz = stencil_nnz(g)
@@ -119,7 +139,22 @@ def stencil27_torch(g: int, device, planes_per_chunk: int = 32):
         cnt = rr.numel()
         rows[pos:pos + cnt] = rr.to(torch.int32)
         cols[pos:pos + cnt] = cc.to(torch.int32)
-        vals[pos:pos + cnt] = torch.where(rr == cc, 26.0, -1.0).to(torch.float64)
+        if perturb_seed is None:
+            vals[pos:pos + cnt] = torch.where(rr == cc, 26.0, -1.0).to(torch.float64)
+        else:
+            lo, hi = torch.minimum(rr, cc), torch.maximum(rr, cc)
+            salt = _as_i64(int(_splitmix64(np.array([perturb_seed], np.uint64))[0]))
+            u = (_splitmix64_torch((lo * n + hi) ^ salt) >> 11) & ((1 << 53) - 1)
+            offv = -(1.0 + 0.1 * (u.to(torch.float64) * (1.0 / 9007199254740992.0)))
+            v = torch.where(rr == cc, torch.zeros_like(offv), offv)
+            Vm = torch.zeros(C.shape, dtype=torch.float64, **kw)
+            Vm[valid] = v
+            diag = torch.zeros(C.shape[0], dtype=torch.float64, **kw)
+            for k in range(27):
+                diag = diag + Vm[:, k].abs()
+            diag = diag + 1.0
+            diag_rep = diag[:, None].expand_as(C)[valid]
+            vals[pos:pos + cnt] = torch.where(rr == cc, diag_rep, v)
         pos += cnt
     assert pos == nnz
     return rows, cols, vals

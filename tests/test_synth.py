@@ -16,6 +16,22 @@ def test_torch_stencil_equals_numpy_stencil(g):
     assert np.array_equal(v, vt.numpy())
 
 
+@pytest.mark.parametrize("g,seed", [(2, 1), (5, 3), (12, 7)])
+def test_torch_perturbed_stencil_equals_numpy(g, seed):
+    """The perturbed stencil built by torch (int64 hash arithmetic) is bit for bit the numpy
+    one: same hash of each unordered pair, same left-to-right diagonal sum."""
+    r, c, v = synth.stencil27_perturbed(g, seed)
+    rt, ct, vt = synth.stencil27_torch(g, "cpu", planes_per_chunk=3, perturb_seed=seed)
+    assert np.array_equal(r, rt.numpy()) and np.array_equal(c, ct.numpy())
+    assert np.array_equal(v.view(np.uint64), vt.numpy().view(np.uint64))
+    # symmetric, strictly diagonally dominant
+    n = g ** 3
+    D = np.zeros((n, n))
+    D[r, c] = v
+    assert np.array_equal(D, D.T)
+    assert np.all(np.diag(D) > np.abs(D - np.diag(np.diag(D))).sum(axis=1))
+
+
 @pytest.mark.parametrize("seed", range(8))
 @pytest.mark.parametrize("backend", ["numpy", "torch"])
 def test_family_recipe(seed, backend):
