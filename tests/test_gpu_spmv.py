@@ -197,8 +197,9 @@ def test_csr_every_kernel_choice(mspv, orc, vec, monkeypatch):
 
 @pytest.mark.parametrize("kernel", ["seg", "vec", "vec512", "rb"])
 def test_coo_every_kernel_choice(mspv, orc, kernel, monkeypatch):
-    """Every COO kernel (lane-sequential 512-entry segments; run-vector 256-entry chunks; 8-row
-    blocks) on shapes that hit their edges: rows spanning lanes and chunks, a row covering many
+    """Every COO kernel (lane-sequential 512-entry segments; run-vector 256-entry chunks; 32-row
+    blocks, here also with rows far above the 128 entries it is chosen for) on shapes that hit
+    their edges: rows spanning lanes and chunks, a row covering many
     chunks, empty rows before, between and after entries (whole empty row blocks), partial
     last lanes and chunks, one entry."""
     monkeypatch.setenv("MSPV_COO_KERNEL", kernel[:3])
