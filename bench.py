@@ -185,21 +185,29 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def time_to_solution(mspv, torch, dev, g, perturb_seed, inner_tol):
+def time_to_solution(mspv, torch, dev, g, perturb_seed, inner_tol, tune=False):
     """Time to a 1e-10 relative residual from x0 = 0 on the g^3 stencil, DIA: FP64 CG against
     FP64-outer mixed precision. Exact values 26 / -1 with b = A 1 (HPCG's right-hand side), or
     the perturbed SPD stencil, whose values FP32 / BF16 do round, with b = A x* for
     x* ~ U[0.5, 1.5) (seed 1): its rows sum to 1, so A 1 = 1 is an eigenvector and b = A 1 would
     converge in one iteration. Each solver runs once untimed, then once timed with CUDA events;
-    max |x - x*| is the error against the exact solution."""
+    max |x - x*| is the error against the exact solution. With `tune`, FP64 CG also runs in the
+    format the run-first tuner picks (every format built and timed, the fastest kept)."""
     n = g ** 3
     r, c, v = synth.stencil27_torch(g, dev, perturb_seed=perturb_seed)
     A = mspv.Matrix.from_coo(n, n, r, c, v)
     del r, c, v
+    tuned = None
+    if tune:
+        tuned, tune_ms = A.tune_format(reps=10)
+        T = None if tuned in ("dia", "coo") else A.convert(tuned)
     D = A.convert("dia")
     D32 = A.convert("dia", "f32")
     D16 = A.convert("dia", "bf16")
-    A.close()
+    if tuned == "coo":
+        T = A
+    else:
+        A.close()
     if perturb_seed is None:
         xstar = torch.ones(n, dtype=torch.float64, device=dev)
     else:
@@ -208,6 +216,8 @@ def time_to_solution(mspv, torch, dev, g, perturb_seed, inner_tol):
     stream = torch.cuda.current_stream()
     modes = (
         ("fp64_cg", lambda xx: D.cg(b, x=xx, tol=1e-10, maxit=20000)),
+        ("fp64_cg_tuner_format", (lambda xx: T.cg(b, x=xx, tol=1e-10, maxit=20000)) if tune and T is not None
+         else None),
         # FP32 values with FP64 arithmetic in the inner CG and its SpMV (FP64 accumulation)
         ("ir_f32_values_fp64_arith", lambda xx: D.cg_ir(D32, b, x=xx, tol=1e-10, inner_tol=1e-5,
                                                         max_outer=40, maxit_inner=20000)),
@@ -222,7 +232,12 @@ def time_to_solution(mspv, torch, dev, g, perturb_seed, inner_tol):
     )
     os.environ["MSPV_CG_CHECK_EVERY"] = "10"
     out = {}
+    if tune:
+        out["tuner"] = {"format": tuned,
+                        "ms_per_spmv": {k: (round(x, 5) if math.isfinite(x) else None) for k, x in tune_ms.items()}}
     for label, fn in modes:
+        if fn is None:
+            continue
         xx = torch.zeros(n, dtype=torch.float64, device=dev)
         fn(xx)
         xx.zero_()
@@ -238,8 +253,9 @@ def time_to_solution(mspv, torch, dev, g, perturb_seed, inner_tol):
                       "max_abs_err": float((xx - xstar).abs().max().item())}
     base = out["fp64_cg"]["ms"]
     for label, rec in out.items():
-        rec["speedup_vs_fp64_cg"] = round(base / rec["ms"], 3)
-    for M in (D, D32, D16):
+        if "ms" in rec:
+            rec["speedup_vs_fp64_cg"] = round(base / rec["ms"], 3)
+    for M in (D, D32, D16) + ((T,) if tune and T is not None else ()):
         M.close()
     return out
 
@@ -455,6 +471,10 @@ def run_mspv(args, world, rank, local):
     if args.tts_grid > 0:
         tts["exact"] = time_to_solution(mspv, torch, dev, args.tts_grid, None, args.ir_inner_tol)
         tts["perturbed"] = time_to_solution(mspv, torch, dev, args.tts_grid, 3, args.ir_inner_tol)
+    tts_large = {}
+    if args.tts_large_grid > 0:
+        tts_large["exact"] = time_to_solution(mspv, torch, dev, args.tts_large_grid, None, args.ir_inner_tol,
+                                              tune=True)
 
     # the FP64 FMA rate of this GPU: the peak of the FP64 (ALU-bound) roofline
     fp64_peak = mspv.fp64_fma_rate()
@@ -481,7 +501,8 @@ def run_mspv(args, world, rank, local):
         "cg": {"ms_per_iter": round(cg_ms_iter, 5),
                "GB_s": round(bm["cg_iter"] / (cg_ms_iter * 1e-3) / 1e9, 1),
                "time_to_1e-10": tt,
-               f"time_to_1e-10_{args.tts_grid}^3": tts},
+               f"time_to_1e-10_{args.tts_grid}^3": tts,
+               f"time_to_1e-10_{args.tts_large_grid}^3": tts_large},
         "convert_s": {"coo_sort_coalesce": round(t_coo, 4), "csr": round(t_csr, 4), "dia": round(t_dia, 4)},
         "roofline": {"kernel": "spmv_dia_kernel<double>", "bound": "alu",
                      "achieved": round(achieved_tf, 4), "peak": round(derived_peak, 4), "unit": "TFLOP/s",
@@ -588,6 +609,21 @@ def run_selector(args, world, rank, local):
                                    **_regret(ms[held][m], pred[m])}
         sel_stats = _regret(ms[held], pred)
         csr_stats = _regret(ms[held], np.ones(int(held.sum()), dtype=np.int64))
+        # The regret above is measured on the timings that made the labels. A second, independent
+        # timing run of the held-out matrices judges the same predictions on fresh timings, and
+        # shows how often the tuner's own pick repeats (near-ties flip).
+        held_seeds = [x["seed"] for x, h in zip(rec, held) if h]
+        ms2 = np.zeros((len(held_seeds), 3))
+        for k, seed in enumerate(held_seeds):
+            fam, n, r, c, v = synth.family_matrix_torch(seed, dev)
+            A = mspv.Matrix.from_coo(n, n, r, c, v)
+            del r, c, v
+            _, t2 = A.tune_format(reps=args.tune_reps)
+            A.close()
+            ms2[k] = [t2[f] for f in FMT]
+        retimed = {**_regret(ms2, pred), "tuner_label_repeats": round(float(np.mean(ms2.argmin(axis=1) ==
+                                                                                 y[held])), 4),
+                   "always_csr_regret": _regret(ms2, np.ones(len(held_seeds), dtype=np.int64))["regret"]}
         t_feat = np.array([x["t_feat"] for x in rec])
         t_tune = np.array([x["t_tune"] for x in rec])
         out = {
@@ -602,6 +638,7 @@ def run_selector(args, world, rank, local):
                        "epochs": args.epochs, "lr": args.lr, "parallelism": f"labels sharded x{world}"},
             "held_out": {**sel_stats, "accuracy": round(float(np.mean(pred == y[held])), 4),
                          "always_csr": csr_stats, "per_family": per_family},
+            "held_out_retimed": retimed,
             "train_accuracy": round(train_acc, 4),
             "label_distribution": {FMT[k]: int(v) for k, v in enumerate(np.bincount(y, minlength=3))},
             "cost_ms_per_matrix": {"features": round(float(t_feat.mean() * 1e3), 3),
@@ -959,6 +996,9 @@ def main():
     ap.add_argument("--ref-cg-iters", type=int, default=1,
                     help="CG iterations per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tts-large-grid", type=int, default=256,
+                    help="step mode: stencil grid of the second time-to-1e-10 block, exact values, FP64 "
+                         "CG also in the run-first tuner's format (0 skips it)")
     ap.add_argument("--tts-grid", type=int, default=192,
                     help="step mode: stencil grid of the time-to-1e-10 block, exact and perturbed "
                          "values (0 skips it)")
