@@ -525,7 +525,7 @@ def run_mspv(args, world, rank, local):
         "gpu_launches": launches_per_step * K,
         "clocks": clk,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host baseline is an N = 1 figure
         out["cpu_baseline"] = cpu_baseline(g, args.cpu_cg_iters)
     if world > 1:
         torch.distributed.destroy_process_group()
