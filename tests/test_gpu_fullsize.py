@@ -3,8 +3,9 @@
 configuration the benchmark times, against the oracle on the whole output; plus the
 separable closed form A x = 27 x - (T (x) T (x) T) x as a size-independent property,
 and 50 FP64 CG iterations against the oracle's. At 192^3 (the mixed-precision workload)
-and 256^3 (the format-selection workload), where the oracle would take minutes, the
-closed form checks every SpMV output and the FP64 residual of each solver's answer."""
+and 256^3 (the format-selection and end-to-end workload), where the oracle's CG would take
+minutes, the closed form checks every SpMV output and the FP64 residual of each solver's
+answer; on the perturbed 192^3 stencil, which has no closed form, the oracle's SpMV does."""
 import numpy as np
 import pytest
 
@@ -142,4 +143,71 @@ def test_256_spmv_closed_form(mspv):
         assert np.all(np.abs(y - want) <= 1e-13 * scale), fmt
         if M is not A:
             M.close()
+    A.close()
+
+
+def test_256_solvers_reach_fp64_residual(mspv):
+    """256^3 (the end-to-end configuration): FP64 CG in DIA, the format the run-first tuner
+    picks there, and the mixed-precision solvers with FP32 and BF16 DIA values (reliable
+    updates; restarted refinement with an FP32 inner CG), each to 1e-10, checked by the FP64
+    residual of the separable closed form and by the error against x = 1 within
+    kappa * relres (kappa ~ 8,923); FP64 CG's count also against the CG bound."""
+    g = 256
+    n, A = stencil_on_device(mspv, g)
+    D = A.convert("dia")
+    b_host, _ = sep_apply(np.ones(n), g)
+    b = torch.from_numpy(b_host).cuda()
+    bn = np.linalg.norm(b_host)
+
+    def check(res, limit):
+        assert res.converged
+        x = res.x.cpu().numpy()
+        ax, _ = sep_apply(x, g)
+        assert np.linalg.norm(b_host - ax) / bn <= 1.2e-10
+        assert np.linalg.norm(x - 1.0) / np.sqrt(n) <= 8923 * 1.2e-10
+        assert res.iters <= limit
+
+    ref = D.cg(b, tol=1e-10, maxit=5000)
+    check(ref, int(np.sqrt(8923) / 2 * np.log(2 / 1e-10)) + 1)
+    for vt in ("f32", "bf16"):
+        L = A.convert("dia", vt)
+        check(D.cg_ru(L, b, tol=1e-10, maxit=5000), int(1.4 * ref.iters))
+        check(D.cg_ir(L, b, tol=1e-10, inner_tol=1e-6, max_outer=30, maxit_inner=5000, inner_fp32=1),
+              int(2.0 * ref.iters))
+        L.close()
+    D.close()
+    A.close()
+
+
+def test_192_perturbed_values_solvers_against_oracle_residual(mspv, orc):
+    """192^3 perturbed SPD stencil, whose values FP32 and BF16 do round (the benchmark's second
+    192^3 matrix): b = A x* for x* ~ U[0.5, 1.5) computed by the oracle's Algorithm 1 on the
+    host; FP64 CG, reliable updates and FP32-inner refinement with FP32 / BF16 values reach a
+    true FP64 residual (the oracle's SpMV again) of 1e-10, and x is within kappa * relres of x*,
+    kappa <= 58.2 from Gershgorin (diagonal = sum |off| + 1, off-diagonals of magnitude <= 1.1)."""
+    g = 192
+    n = g ** 3
+    r, c, v = synth.stencil27_torch(g, "cuda", perturb_seed=3)
+    O = orc.Matrix(orc.COO, n, n, r.numel(), ai=r.cpu().numpy(), aj=c.cpu().numpy(), av=v.cpu().numpy())
+    A = mspv.Matrix.from_coo(n, n, r, c, v)
+    del r, c, v
+    D = A.convert("dia")
+    xs = synth.uniform_x(n, 1) + 0.5
+    b_host = orc.spmv(O, xs)
+    b = torch.from_numpy(b_host).cuda()
+    bn = np.linalg.norm(b_host)
+
+    def check(res):
+        assert res.converged
+        x = res.x.cpu().numpy()
+        assert np.linalg.norm(b_host - orc.spmv(O, x)) / bn <= 1.2e-10
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 58.2 * 1.2e-10
+
+    check(D.cg(b, tol=1e-10, maxit=5000))
+    for vt in ("f32", "bf16"):
+        L = A.convert("dia", vt)
+        check(D.cg_ru(L, b, tol=1e-10, maxit=5000))
+        check(D.cg_ir(L, b, tol=1e-10, inner_tol=1e-6, max_outer=30, maxit_inner=5000, inner_fp32=1))
+        L.close()
+    D.close()
     A.close()
