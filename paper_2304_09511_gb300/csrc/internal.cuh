@@ -246,7 +246,7 @@ struct mspv_matrix {
     mspv::CooCarry* carry = nullptr;   // COO: per-window carries
     int64_t nchunks = 0;               // COO chunks of kCooVecChunk entries
     int32_t coo_kernel = 0;            // COO: 0 lane-sequential segments, 1 run-vector, 2 row blocks (choose_coo_kernel)
-    int32_t* coo_rb = nullptr;         // COO row-block kernel: first entry of every 8-row block, nrb + 1 entries
+    int32_t* coo_rb = nullptr;         // COO row-block kernel: first entry of every 32-row block, nrb + 1 entries
     int64_t coo_nrb = 0;
     int32_t coo_chunk = 256;           // run-vector kernel: entries per warp (256; MSPV_COO_CHUNK=512)
     int32_t* row_block = nullptr;      // CSR: first row of each window, nblocks + 1 entries

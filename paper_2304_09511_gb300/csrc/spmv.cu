@@ -1239,9 +1239,10 @@ int32_t choose_csr_vector(double mean, double stdev, int32_t maxlen) {
         int v = std::atoi(s);
         if (v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) return v;
     }
-    // V lanes per row: 4 for short rows (coalesced 32-byte segments, two FP64
-    // shuffle-adds per 8 rows), wider as rows grow; rows longer than 32 V entries are
-    // reduced by a CTA each. The staged kernels (0) are selected only explicitly.
+    // V lanes per row: 4 for short rows (coalesced 32-byte segments; a warp's 32 rows joined
+    // by a reduce-scatter of 3 FP64 adds per lane), wider as rows grow; rows longer than
+    // 32 V entries are reduced by a CTA each. The staged kernels (0) are selected only
+    // explicitly.
     if (mean <= 48.0) return 4;
     if (mean <= 96.0) return 8;
     if (mean <= 192.0) return 16;
