@@ -130,3 +130,33 @@ def test_split_rejects_bad_arguments(mspv):
         D.split_columns(2)
     L, R = A.split_columns(0)
     assert L.info["nnz"] == 0 and R.info["nnz"] == 2 and R.shape == (4, 6)
+
+
+@pytest.mark.parametrize("local_fmt,remote_fmt", [("dia", "coo"), ("csr", "csr")])
+def test_zslab_partition_on_one_gpu(mspv, orc, local_fmt, remote_fmt):
+    """The row-block partition of the distributed HPCG run through the library on one GPU: the
+    40^3 stencil cut into 4 z-slabs, each slab's matrix (own columns, then ghost columns by
+    first appearance) split by the library, y_s = A_local x_s then y_s += A_remote x_ghost;
+    the slabs together equal the whole matrix's SpMV bit for bit (integer data and x, so every
+    partial sum is exact)."""
+    from test_partition_cpu import slab_matrix
+    g, P = 40, 4
+    n = g ** 3
+    rows, cols, vals = synth.stencil27(g)
+    x = np.random.default_rng(7).integers(-4, 5, n).astype(np.float64)
+    W = mspv.Matrix.from_coo(n, n, dev(rows), dev(cols), dev(vals)).convert("dia")
+    want = W.spmv(dev(x)).cpu().numpy()
+    assert np.array_equal(want, orc.spmv(orc.Matrix(orc.COO, n, n, rows.size, ai=rows, aj=cols, av=vals), x))
+    cuts = np.linspace(0, g, P + 1).round().astype(int)
+    got = []
+    for s in range(P):
+        z0, z1 = cuts[s], cuts[s + 1]
+        r, c, v, n_s, ghosts = slab_matrix(g, z0, z1, rows, cols, vals)
+        S = mspv.Matrix.from_coo(n_s, n_s + ghosts.size, dev(r), dev(c), dev(v))
+        L, R = S.split_columns(n_s)
+        L = L if local_fmt == "coo" else L.convert(local_fmt)
+        R = R if remote_fmt == "coo" else R.convert(remote_fmt)
+        y = L.spmv(dev(x[z0 * g * g:z1 * g * g]))
+        R.spmv_add(dev(x[ghosts]), y)
+        got.append(y.cpu().numpy())
+    assert np.array_equal(np.concatenate(got), want)
