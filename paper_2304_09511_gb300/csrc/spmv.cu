@@ -1328,7 +1328,7 @@ static int64_t dia_strip_rows(int vt, bool f32) {
     }
 }
 
-static int64_t csr_grid_for(const mspv_matrix* A);
+static int64_t csr_grid_for(const mspv_matrix* A, bool f32);
 
 // CTAs of the fused-dot SpMV launch in FP64 or FP32 arithmetic: the number of p.q partials
 // it writes, which the CG's alpha kernel sums. Only DIA launches differ between the two
@@ -1341,7 +1341,7 @@ int64_t spmv_partials_count(const mspv_matrix* A, bool f32) {
             return g < 1 ? 1 : g;
         }
         case MSPV_CSR:
-            return csr_grid_for(A);
+            return csr_grid_for(A, f32);
         default:
             return vector_grid(A->nrows);
     }
@@ -1404,18 +1404,21 @@ static int64_t csr_warp_grid(int32_t nrows) {
 }
 
 // CTAs of the V-lane kernels (a CTA covers kThreads rows for V <= 8, kThreads / V rows for
-// wider rows); with a dot-product epilogue (inside CG) at most two waves of 8 CTAs per SM, the
-// warps striding over the rows.
-static int64_t csr_vector_grid(const mspv_matrix* A, bool capped) {
+// wider rows). With a dot-product epilogue (inside CG) the grid is capped, so the scalar kernels
+// sum few partials, and the warps stride over the rows: 12 CTAs per SM in FP64 arithmetic (the
+// striding kernel holds 6 CTAs per SM at its 40 registers, so two whole waves; 16 per SM made a
+// ragged third wave, 0.58 vs 0.54 ms per FP64 CG iteration at 192^3), 24 per SM in FP32
+// arithmetic (the inner solver's kernels: 24 measured faster than 12 or 16, 192^3 BF16 values).
+static int64_t csr_vector_grid(const mspv_matrix* A, bool capped, bool f32) {
     const int64_t lanes_per_row = A->csr_vector <= 8 ? 1 : A->csr_vector;
     int64_t g = ((int64_t)A->nrows * lanes_per_row + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)num_sms() * 8 * 2;
+    const int64_t cap = (int64_t)num_sms() * (f32 ? 24 : 12);
     if (capped && g > cap) g = cap;
     return g < 1 ? 1 : g;
 }
 
-static int64_t csr_grid_for(const mspv_matrix* A) {
-    if (A->csr_vector != 0) return csr_vector_grid(A, true) + A->nlong;
+static int64_t csr_grid_for(const mspv_matrix* A, bool f32) {
+    if (A->csr_vector != 0) return csr_vector_grid(A, true, f32) + A->nlong;
     if (A->csr_block) return A->nblocks;
     if (A->value_type == MSPV_F64) return csr_warp_grid<double, double>(A->nrows);
     // FP32/BF16 values run the FP64-arithmetic or FP32-arithmetic instantiation; both
@@ -1446,7 +1449,7 @@ static void launch_csr(const mspv_matrix* A, const T* x, T* y, cudaStream_t s, D
         return;
     }
     const bool capped = ep.partials != nullptr;
-    const unsigned grid = (unsigned)csr_vector_grid(A, capped);
+    const unsigned grid = (unsigned)csr_vector_grid(A, capped, sizeof(T) == 4);
     const int32_t long_len = A->nlong > 0 ? 32 * V : INT_MAX;
 #define MSPV_CSR_CASE(VV, KERNEL)                                                              \
     case VV:                                                                                   \
