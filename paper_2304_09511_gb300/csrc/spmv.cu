@@ -1403,17 +1403,45 @@ static int64_t csr_warp_grid(int32_t nrows) {
     return g < 1 ? 1 : g;
 }
 
+// Resident CTAs per SM of the striding 32-row CSR kernel (the grid inside CG) for a value type
+// and arithmetic, from the occupancy calculator; the V = 4 instantiation stands for every lane
+// width.
+template <typename VT, typename T>
+static int csr_stride_ctas_per_sm() {
+    static const int k = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, spmv_csr_rows32_kernel<VT, T, 4, true>, kThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            b = 6;
+        return b;
+    }();
+    return k;
+}
+
+static int csr_stride_ctas_per_sm(int vt, bool f32) {
+    switch (vt) {
+        case MSPV_F64: return csr_stride_ctas_per_sm<double, double>();   // FP32 arithmetic needs FP32/BF16 values
+        case MSPV_F32: return f32 ? csr_stride_ctas_per_sm<float, float>() : csr_stride_ctas_per_sm<float, double>();
+        default:
+            return f32 ? csr_stride_ctas_per_sm<__nv_bfloat16, float>()
+                       : csr_stride_ctas_per_sm<__nv_bfloat16, double>();
+    }
+}
+
 // CTAs of the V-lane kernels (a CTA covers kThreads rows for V <= 8, kThreads / V rows for
 // wider rows). With a dot-product epilogue (inside CG) the grid is capped, so the scalar kernels
-// sum few partials, and the warps stride over the rows: 12 CTAs per SM in FP64 arithmetic (the
-// striding kernel holds 6 CTAs per SM at its 40 registers, so two whole waves; 16 per SM made a
-// ragged third wave, 0.58 vs 0.54 ms per FP64 CG iteration at 192^3), 24 per SM in FP32
-// arithmetic (the inner solver's kernels: 24 measured faster than 12 or 16, 192^3 BF16 values).
+// sum few partials, and the warps stride over the rows: two whole waves of the striding kernel in
+// FP64 arithmetic, three in FP32 arithmetic. A fixed 16 CTAs per SM made a ragged third wave of
+// the 40-register FP64 kernel, which holds 6 CTAs per SM (0.58 vs 0.54 ms per FP64 CG iteration
+// at 192^3); the FP32-arithmetic kernels of the inner solver measured fastest at three waves.
 static int64_t csr_vector_grid(const mspv_matrix* A, bool capped, bool f32) {
     const int64_t lanes_per_row = A->csr_vector <= 8 ? 1 : A->csr_vector;
     int64_t g = ((int64_t)A->nrows * lanes_per_row + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)num_sms() * (f32 ? 24 : 12);
-    if (capped && g > cap) g = cap;
+    if (capped) {
+        const int64_t cap = (int64_t)num_sms() * csr_stride_ctas_per_sm(A->value_type, f32) * (f32 ? 3 : 2);
+        if (g > cap) g = cap;
+    }
     return g < 1 ? 1 : g;
 }
 
