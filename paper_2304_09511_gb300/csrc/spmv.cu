@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_vector_kernel(
             if (e - s > long_len) {
                 mine = false;   // written by the long-row kernel
             } else {
-                for (int32_t j = s + lane; j < e; j += V)
+                for (int64_t j = s + lane; j < e; j += V)
                     sum = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), sum);
             }
         }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_long_kernel(
     const int32_t row = long_rows[blockIdx.x];
     const int32_t s = __ldg(irp + row), e = __ldg(irp + row + 1);
     T part = T(0);
-    for (int32_t j = s + threadIdx.x; j < e; j += kThreads)
+    for (int64_t j = s + threadIdx.x; j < e; j += kThreads)
         part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
     const T sum = block_sum_t(part, s_red);
     if (threadIdx.x == 0) {
@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(kThreads) spmv_csr_stage_kernel(
                     continue;
                 }
                 T part = T(0);
-                for (int32_t j = a + threadIdx.x; j < b; j += kThreads)
+                for (int64_t j = a + threadIdx.x; j < b; j += kThreads)
                     part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
                 const T sum = block_sum_t(part, s_red_t);
                 if (threadIdx.x == 0) {
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
             for (int q = 0; q < nr; ++q) {
                 const int32_t a = __shfl_sync(0xffffffffu, myb, q), b = __shfl_sync(0xffffffffu, mye, q);
                 T part = T(0);
-                for (int32_t j = a + lane; j < b; j += 32)
+                for (int64_t j = a + lane; j < b; j += 32)
                     part = fma_t(convert_value<T>(__ldcs(av + j)), __ldg(x + __ldcs(aj + j)), part);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -745,8 +745,8 @@ __global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
             continue;
         }
         T sum = T(0);
-        for (int32_t c0 = s; c0 < e; c0 += WCAP) {
-            const int len = (e - c0 < WCAP) ? e - c0 : WCAP;
+        for (int64_t c0 = s; c0 < e; c0 += WCAP) {
+            const int len = (int)((e - c0 < WCAP) ? e - c0 : WCAP);
             for (int k = lane; k < len; k += 32) {
                 if constexpr (sizeof(VT) == sizeof(T)) cp_async<sizeof(T)>(a_s + k, av + c0 + k);
                 else if constexpr (sizeof(VT) == 4) cp_async4(a_s + k, av + c0 + k);
@@ -757,8 +757,8 @@ __global__ void __launch_bounds__(NT) spmv_csr_warp_kernel(
             for (int k = lane; k < len; k += 32) cp_async<sizeof(T)>(x_s + k, x + slot_idx[STRIDE * k]);
             cp_async_wait_all();
             __syncwarp();
-            const int b = (myb - c0 > 0) ? myb - c0 : 0;
-            const int en = (mye - c0 < len) ? mye - c0 : len;
+            const int b = (int)((myb - c0 > 0) ? myb - c0 : 0);
+            const int en = (int)((mye - c0 < len) ? mye - c0 : len);
             if (has_row && b < en) {
                 int j = b;
                 for (; j + 4 <= en; j += 4) {
@@ -1113,9 +1113,11 @@ __global__ void __launch_bounds__(kThreads, 3) spmv_coo_seg_kernel(
     const int cnt = (len - b >= kCooSegPer) ? kCooSegPer : (len - b > 0 ? len - b : 0);
     const int64_t e0 = c0 + b;
 
-    // Sequential pass. `cur` starts at the row of the entry before the lane's first one, so
-    // the empty rows in between are zero-filled by the same row-change step. A lane without
-    // entries acts as a single run of the chunk's last row with sum 0 (transparent below).
+    // Sequential pass over the lane's entries: each row change closes the run before it (the
+    // lane's first run is kept as `head` for the joins below, later runs are written at once).
+    // Rows without entries are not written here (the launcher zero-fills y first when the
+    // matrix has any). A lane without entries acts as a single run of the chunk's last row
+    // with sum 0 (transparent below).
     int32_t cur = chunk_last, first = chunk_last;
     T head = T(0), sum = T(0);
     bool closed = false;   // the lane's first run has ended inside the lane
