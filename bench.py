@@ -94,6 +94,27 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def copy_rate_gbs(torch, dev, elems: int = 1 << 30, repeats: int = 10) -> float:
+    """Device-to-device copy rate of this GPU: read + write bytes of one copy of `elems` BF16
+    values over its CUDA-event time, the fastest of `repeats` (after two untimed copies). The
+    STREAM-style figure, measured live beside the HBM peak the line is judged against."""
+    a = torch.ones(elems, dtype=torch.bfloat16, device=dev)
+    b = torch.empty_like(a)
+    s = torch.cuda.current_stream(dev)
+    best = float("inf")
+    for k in range(repeats + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        b.copy_(a)
+        e1.record(s)
+        e1.synchronize()
+        if k >= 2:
+            best = min(best, e0.elapsed_time(e1))
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * 2 * elems / (best * 1e-3) / 1e9
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -476,8 +497,11 @@ def run_mspv(args, world, rank, local):
         tts_large["exact"] = time_to_solution(mspv, torch, dev, args.tts_large_grid, None, args.ir_inner_tol,
                                               tune=True)
 
-    # the FP64 FMA rate of this GPU: the peak of the FP64 (ALU-bound) roofline
+    # the FP64 FMA rate of this GPU: the peak of the FP64 (ALU-bound) roofline; and its copy rate
     fp64_peak = mspv.fp64_fma_rate()
+    copy_gbs = copy_rate_gbs(torch, dev)
+    for f in ("coo", "csr", "dia"):
+        per_format[f]["frac_of_live_copy"] = round(per_format[f]["GB_s"] / copy_gbs, 4)
 
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(clk["sm_max_mhz"]) if clk and clk.get("sm_max_mhz") else 2070.0
@@ -498,6 +522,7 @@ def run_mspv(args, world, rank, local):
                    "l2": "inputs larger than L2 (matrices 486-925 MB per format; no flush)",
                    "parallelism": f"replicas x{world}"},
         "per_format": per_format,
+        "hbm_peak": {"GB_s": peaks["hbm_gbs"], "source": peaks["source"], "copy_measured_live": round(copy_gbs, 1)},
         "cg": {"ms_per_iter": round(cg_ms_iter, 5),
                "GB_s": round(bm["cg_iter"] / (cg_ms_iter * 1e-3) / 1e9, 1),
                "time_to_1e-10": tt,
@@ -519,7 +544,9 @@ def run_mspv(args, world, rank, local):
                                        "on the 128^3 stencil (scaled by rows at other grids)",
                      "flops_per_launch": 2 * nnz, "bytes_per_launch": bm["dia"],
                      "hbm": {"achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                             "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"]}},
+                             "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "peak_source": peaks["source"],
+                             "copy_measured_live": round(copy_gbs, 1),
+                             "frac_of_live_copy": round(achieved_gbs / copy_gbs, 4)}},
         "e2e": {"value": round(e2e_value, 1), "unit": "GB/s", "ms_per_step": round(e2e_ms, 4),
                 "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 32 * n},
         "gpu_launches": launches_per_step * K,
