@@ -97,7 +97,7 @@ def load_peaks() -> dict:
 def copy_rate_gbs(torch, dev, elems: int = 1 << 30, repeats: int = 10) -> float:
     """Device-to-device copy rate of this GPU: read + write bytes of one copy of `elems` BF16
     values over its CUDA-event time, the fastest of `repeats` (after two untimed copies). The
-    STREAM-style figure, measured live beside the HBM peak the line is judged against."""
+    STREAM-style figure, measured live beside the HBM peak that the fractions are taken of."""
     a = torch.ones(elems, dtype=torch.bfloat16, device=dev)
     b = torch.empty_like(a)
     s = torch.cuda.current_stream(dev)
