@@ -963,8 +963,11 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_vec_kernel(
 // (rows32_sum, 4 lanes per row, reduce-scatter). Rows of the block without entries are
 // written as 0 (left as they are for y += A x). For rows of at most 128 entries (longer ones
 // take the segment kernel).
+// The kernel waits on memory latency, so it is held to 32 registers for 8 CTAs per SM (block
+// positions in 32 bits; a few bytes spill): 157.7-158.6 vs 161.7-162.7 us at 128^3 and 494-495
+// vs 512 us at 192^3 against 40 registers and 6 CTAs.
 template <typename VT, typename T>
-__global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
+__global__ void __launch_bounds__(kThreads, 8) spmv_coo_rb_kernel(
     int32_t nrows, int64_t nnz, const int32_t* __restrict__ ai, const int32_t* __restrict__ aj,
     const VT* __restrict__ av, const int32_t* __restrict__ rb, int64_t nrb, const T* __restrict__ x,
     T* __restrict__ y, const CgState* st, bool acc) {
@@ -976,37 +979,40 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
     __shared__ int32_t s_start[kThreads / 32][kCooRbRows];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t b = (int64_t)blockIdx.x * (kThreads / 32) + w;
-    if (b >= nrb) return;   // whole warp
-    const int64_t row0 = b * kCooRbRows;   // 64-bit: the last block may reach past 2^31 - 1
-    const int64_t e0 = __ldg(rb + b);
-    const int64_t e1 = __ldg(rb + b + 1);
+    // 32-bit positions: entries lie below 2^31, so an entry index plus the 2,048 entries one
+    // round reads past it, and a block's first row, fit in 32 unsigned bits.
+    const uint32_t b = blockIdx.x * (kThreads / 32) + w;
+    if ((int64_t)b >= nrb) return;   // whole warp
+    const uint32_t row0 = b * kCooRbRows;
+    const uint32_t e0 = (uint32_t)__ldg(rb + b);
+    const uint32_t e1 = (uint32_t)__ldg(rb + b + 1);
+    const uint32_t unnz = (uint32_t)nnz;
     const int cnt = (int)(e1 - e0);
     int32_t* start = s_start[w];
     start[lane] = -1;
     __syncwarp();
     // 16-byte groups from the multiple of 4 at or below e0; entries outside [e0, e1) are read
     // (when below nnz) but not marked. ai's allocation starts 256-byte aligned.
-    const int64_t a0 = e0 & ~(int64_t)3;
+    const uint32_t a0 = e0 & ~3u;
     constexpr int kHeld = 4;   // groups loaded together: 512 entries (two rounds for 32 stencil rows)
-    int32_t last = (int32_t)(row0 - 1);   // the row before the first group (a row below the block)
-    for (int64_t g0 = a0; g0 < e1; g0 += 128 * kHeld) {
+    int32_t last = (int32_t)row0 - 1;   // the row before the first group (a row below the block)
+    for (uint32_t g0 = a0; g0 < e1; g0 += 128 * kHeld) {
         int4 v[kHeld];
 #pragma unroll
         for (int q = 0; q < kHeld; ++q) {
-            const int64_t g = g0 + 128 * q + 4 * lane;
-            if (g + 3 < nnz) {
+            const uint32_t g = g0 + 128 * q + 4 * lane;
+            if (g + 3 < unnz) {
                 v[q] = __ldg(reinterpret_cast<const int4*>(ai + g));
             } else {
-                v[q].x = g < nnz ? __ldg(ai + g) : INT_MAX;
-                v[q].y = g + 1 < nnz ? __ldg(ai + g + 1) : INT_MAX;
-                v[q].z = g + 2 < nnz ? __ldg(ai + g + 2) : INT_MAX;
+                v[q].x = g < unnz ? __ldg(ai + g) : INT_MAX;
+                v[q].y = g + 1 < unnz ? __ldg(ai + g + 1) : INT_MAX;
+                v[q].z = g + 2 < unnz ? __ldg(ai + g + 2) : INT_MAX;
                 v[q].w = INT_MAX;
             }
         }
 #pragma unroll
         for (int q = 0; q < kHeld; ++q) {
-            const int64_t g = g0 + 128 * q + 4 * lane;
+            const uint32_t g = g0 + 128 * q + 4 * lane;
             int32_t prev = __shfl_up_sync(FULL, v[q].w, 1);
             if (lane == 0) prev = last;
             last = __shfl_sync(FULL, v[q].w, 31);
@@ -1014,7 +1020,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const int32_t pr = c == 0 ? prev : r[c - 1];
-                if (g + c >= e0 && g + c < e1 && r[c] != pr) start[(int)(r[c] - row0)] = (int)(g + c - e0);
+                if (g + c >= e0 && g + c < e1 && r[c] != pr) start[(int)((uint32_t)r[c] - row0)] = (int)(g + c - e0);
             }
         }
     }
@@ -1038,7 +1044,7 @@ __global__ void __launch_bounds__(kThreads) spmv_coo_rb_kernel(
     });
     const int rr = R * sub + lane / V;
     const bool has = __shfl_sync(FULL, mylen, rr) > 0;
-    const int64_t row = row0 + rr;
+    const int64_t row = (int64_t)row0 + rr;
     if (row < nrows) {
         if (has) store_y(y, row, sum, acc);
         else zero_y(y, row, acc);
