@@ -13,7 +13,7 @@
 //   4. (one CTA) rho' = r.r; convergence test, iteration count, beta = rho' / rho;
 //   5. x += alpha p, then p = r + beta p (one pass over p).
 // Every scalar lives in a device CgState. Once `done` is set all kernels return at
-// entry, so the host may launch past convergence and polls the state only every
+// entry, so the host may launch past convergence and polls the state only after every
 // MSPV_CG_CHECK_EVERY iterations. Reductions are deterministic (fixed order) and use
 // no fence or atomic: on GB300 a fused last-CTA reduction (fence + atomic ticket in
 // every CTA) measured +16 us on a 60 us SpMV, more than two extra tiny launches.
@@ -264,6 +264,13 @@ __global__ void axpy1_kernel(int64_t n, double* __restrict__ x, const double* __
         x[i] += d[i];
 }
 
+// x = 0 when the start kernel found b = 0 (it then also marked the solve done).
+__global__ void zero_if_b_zero_kernel(double* __restrict__ x, int64_t n, const CgState* st) {
+    if (st->bnorm != 0.0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0.0;
+}
+
 __global__ void zero_kernel(double* __restrict__ v, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = 0.0;
@@ -477,11 +484,10 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
     const bool pdl = use_pdl();
     const DotEpilogue ep{w.st, w.partials, pdl};
     const double tol = hst->tol;
+    // Launch first and poll after each batch: the first batch follows the set-up kernels on the
+    // stream without a host round trip (launches past a stop return at entry).
     int32_t launched = 0;
     for (;;) {
-        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hst->done || launched >= maxit) break;
         const int32_t batch = poll_batch(tol, maxit - launched);
         for (int32_t k = 0; k < batch; ++k) {
             MSPV_TRY(spmv(p, q, ep));
@@ -493,6 +499,9 @@ static mspv_status cg_iterate(mspv_matrix* A, V* x, V* r, V* p, V* q, int32_t ma
         }
         MSPV_CUDA_TRY(cudaGetLastError());
         launched += batch;
+        MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hst->done || launched >= maxit) break;
     }
     return MSPV_OK;
 }
@@ -523,19 +532,15 @@ mspv_status cg_solve(mspv_matrix* A, const double* b, double* x, double tol, int
     cg_init_kernel<<<Gi, kThreads, 0, s>>>(n, b, w.q, w.r, w.p, w.partials, w.partials + half);
     MSPV_SCALAR_LAUNCH(false, cg_start_kernel, (int64_t)Gi, s, (const double*)w.partials,
                        (const double*)(w.partials + half), (int64_t)Gi, w.st);
+    // b = 0: the start kernel marks the solve done and the solution is 0 (decided on the device,
+    // so the iterations follow without a host round trip)
+    zero_if_b_zero_kernel<<<(unsigned)vec_grid(n), kThreads, 0, s>>>(x, n, w.st);
     MSPV_CUDA_TRY(cudaGetLastError());
-    MSPV_CUDA_TRY(cudaMemcpyAsync(hst, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-    MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hst->bnorm == 0.0) {   // b = 0: the solution is 0
-        zero_kernel<<<(unsigned)vec_grid(n), kThreads, 0, s>>>(x, n);
-        MSPV_CUDA_TRY(cudaGetLastError());
-        MSPV_CUDA_TRY(cudaStreamSynchronize(s));
-        return MSPV_OK;
-    }
     MSPV_TRY(cg_iterate(
         A, x, w.r, w.p, w.q, maxit, s,
         [&](const double* pp, double* qq, DotEpilogue ep) { return launch_spmv(A, pp, qq, s, ep); },
         cg_update_kernel, cg_pupdate_kernel, Gu, Gp));
+    if (hst->bnorm == 0.0) return MSPV_OK;   // x = 0, no iterations, relres 0
     if (iters) *iters = hst->iters;
     if (relres) *relres = std::sqrt(hst->rho) / hst->bnorm;
     switch (hst->phase) {
