@@ -92,6 +92,7 @@ class Matrix:
 
     def __init__(self, handle: int):
         self._h = ctypes.c_void_p(handle)
+        self._shape = None   # (nrows, ncols), fixed for the handle's life; read once
 
     # -- lifecycle ---------------------------------------------------------------
     @classmethod
@@ -142,8 +143,10 @@ class Matrix:
 
     @property
     def shape(self):
-        i = self.info
-        return i["nrows"], i["ncols"]
+        if self._shape is None:
+            i = self.info
+            self._shape = (i["nrows"], i["ncols"])
+        return self._shape
 
     def export(self) -> dict:
         """Stored structure copied to host numpy arrays (values widened to float64)."""
