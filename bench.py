@@ -403,8 +403,9 @@ def run_mspv(args, world, rank, local):
         "seg" if inf["row_max"] > 128 else ("rb" if inf["nnz"] >= 4 * inf["nrows"] else "vec"))
     chunk = 512 if coo_kernel == "seg" else 256
     coo_launches = 1 if coo_kernel == "rb" else 1 + (1 if (nnz + chunk - 1) // chunk > 1 else 0)
-    # CG: SpMV + init + start, then per iteration SpMV (DIA: 1 kernel), alpha, update, beta, p-update
-    launches_per_step = coo_launches + 1 + 1 + (3 + 5 * args.cg_iters)
+    # CG: SpMV + init + start + the b = 0 check, then per iteration SpMV (DIA: 1 kernel), alpha,
+    # update, beta, p-update
+    launches_per_step = coo_launches + 1 + 1 + (4 + 5 * args.cg_iters)
 
     # end to end through the public API with host buffers: every step copies its x and b from
     # pinned host memory and reads the three SpMV results and the CG solution back, all inside
