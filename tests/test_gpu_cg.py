@@ -132,6 +132,11 @@ def test_cg_special_cases(mspv):
     res = A.cg(torch.zeros(n, dtype=torch.float64, device="cuda"),
                x=torch.ones(n, dtype=torch.float64, device="cuda"), tol=1e-10, maxit=10)
     assert res.converged and res.iters == 0 and torch.all(res.x == 0)
+    # the same with a fixed iteration count (tol = 0): the b = 0 decision is the device's, and
+    # the iterations launched behind it do nothing
+    res = A.cg(torch.zeros(n, dtype=torch.float64, device="cuda"),
+               x=torch.ones(n, dtype=torch.float64, device="cuda"), tol=0.0, maxit=300)
+    assert res.converged and res.iters == 0 and torch.all(res.x == 0)
     # iteration limit -> ENOTCONV with the last iterate
     b = torch.ones(n, dtype=torch.float64, device="cuda")
     res = A.cg(b, tol=1e-14, maxit=3)
