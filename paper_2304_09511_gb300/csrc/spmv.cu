@@ -15,7 +15,7 @@
 //      outer-loop SVE vectorisation (Sec. III), with warp lanes in place of SVE lanes.
 //      The FP32-arithmetic kernel reads one x window per run of consecutive offsets, at
 //      4 rows per thread for FP32 values and 8 (one 16-byte value load per diagonal,
-//      128-thread CTAs) for BF16 values.
+//      kept packed until its FMAs) for BF16 values.
 //  CSR (Algorithm 2): V lanes per row (V = 4 for short rows, chosen from the row-length
 //      statistics). Up to V = 8 a warp owns 32 rows, runs V passes of 32 / V rows with
 //      lane-strided FMAs and joins the passes' partial sums with one reduce-scatter
@@ -228,10 +228,11 @@ __device__ __forceinline__ void dia_f32_fma(const float (&a)[RPT], const float (
     for (int r = 0; r < RPT; ++r) acc[r] = fmaf(a[r], w[M + r], acc[r]);
 }
 
-// CTA size of the FP32-arithmetic DIA kernel: 128 threads at 8 rows per thread (BF16 values,
-// 48 registers), 256 at 4 (FP32 values); a CTA covers 1,024 rows either way.
+// CTA size of the FP32-arithmetic DIA kernel: 256 threads, 8 rows per thread with BF16 values
+// (48 registers, 2,048 rows per CTA) and 4 with FP32 values (1,024 rows). Inside CG the BF16
+// strips of 2,048 rows halve the partials the alpha kernel sums against 128-thread CTAs of
+// 1,024 rows (same SpMV time; reliable updates at 192^3 48.5 vs 49.1 ms).
 template <typename VT> struct DiaF32Shape { static constexpr int NT = kThreads; };
-template <> struct DiaF32Shape<__nv_bfloat16> { static constexpr int NT = 128; };
 
 template <typename VT>
 __global__ void __launch_bounds__(DiaF32Shape<VT>::NT) spmv_dia_f32_kernel(
