@@ -135,10 +135,11 @@ MSPV_API mspv_status mspv_spmv(mspv_matrix_t A, const double* x, double* y, void
  * sqrt(rho) / ||b|| (the recursively updated residual).
  * Returns OK, ENOTCONV (maxit reached with tol > 0; x holds the last iterate) or
  * EBREAKDOWN (p.q <= 0 or non-finite alpha; x holds the last completed iterate).
- * Vector work runs on the device with device-resident scalars; the host polls a
- * convergence flag every MSPV_CG_CHECK_EVERY iterations (default 10; with tol <= 0, a fixed
- * count, every 256 iterations unless that variable is set);
- * launches past convergence are no-ops, so results do not depend on that interval.
+ * Vector work runs on the device with device-resident scalars (||b|| = 0 included); the
+ * host launches batches of MSPV_CG_CHECK_EVERY iterations (default 10; with tol <= 0, a
+ * fixed count, up to 256 unless that variable is set) and reads the convergence flag after
+ * each batch; launches past convergence are no-ops, so results do not depend on that
+ * interval. The call returns once the solve has ended (it synchronises the stream).
  * Workspace (3 vectors + reduction partials) is allocated once per handle.
  */
 MSPV_API mspv_status mspv_cg_solve(mspv_matrix_t A, const double* b, double* x, double tol,
