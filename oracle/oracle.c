@@ -14,17 +14,20 @@
  * What each function follows:
  *   orc_coo_canonicalize  COO storage (Sec. II-B-1). The paper puts no order on
  *                         COO; the canonical form sorts by (row, col), stable,
- *                         and sums duplicates in input order (reading (c)2).
+ *                         and sums duplicates in input order (a reading: the
+ *                         paper fixes neither).
  *   orc_coo_to_csr        CSR row pointers (Sec. II-B-2): irp(i) = first entry of
  *                         row i, irp(nrows) = NNZ.
  *   orc_dia_offsets,
  *   orc_coo_to_dia        DIA storage (Sec. II-B-3): one column of AV per
  *                         diagonal, DOFF holds each diagonal's offset col-row,
  *                         out-of-matrix slots zero. Layout here is diagonal-major
- *                         AV[j*npad + i] (reading (c)4).
+ *                         AV[j*npad + i], npad = n rounded up to 32 (a reading:
+ *                         the paper's SVE code indexes AV row-major).
  *   orc_dia_to_coo,
  *   orc_csr_to_coo        inverse maps, used by the round-trip pins.
- *   orc_spmv_coo          Algorithm 1, with y cleared first (reading (c)5).
+ *   orc_spmv_coo          Algorithm 1, with y cleared first (a reading: the
+ *                         printed += is taken as an overwrite of y).
  *   orc_spmv_csr          Algorithm 2.
  *   orc_spmv_dia          Algorithm 3 (bounds check 0 <= k < N).
  *   orc_round_values      storage rounding of matrix values to FP32 / BF16

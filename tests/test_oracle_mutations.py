@@ -1,11 +1,13 @@
-"""Planted mistakes in the oracle's mixed-precision solvers must fail their pins.
+"""Planted mistakes in the oracle must fail its pins.
 
 Each case compiles a copy of ``oracle/oracle.c`` with one plausible mistake written into
 it, loads that copy in place of the oracle library for the duration of the test, and
-runs the pins of ``test_oracle_pins`` against it: at least one must fail. This checks
-that the pins of refinement and of reliable updates (which the paper does not define and
-which therefore have no printed values to compare with) see a swapped matrix, a dropped
-carry or a wrong sign. CPU only; needs gcc.
+runs the pins of ``test_oracle_pins`` against it: at least one must fail. This checks that
+the pins see the mistakes a restatement of the method could plausibly make: in the three
+SpMV algorithms (an overwrite for an accumulation, an entry skipped, an off-by-one bound),
+in CG (an inverted beta, a wrong vector or sign in an update) and in refinement and reliable
+updates, which the paper does not define and which therefore have no printed values to
+compare with (a swapped matrix, a dropped carry, a wrong sign). CPU only; needs gcc.
 """
 from __future__ import annotations
 
@@ -82,4 +84,47 @@ def test_reliable_update_pins_catch_planted_mistake(tmp_path, monkeypatch, name)
     caught = (_fails(lambda: pins.test_cg_ru_iterates_match_exact_rational_cg(oracle))
               or _fails(lambda: pins.test_cg_ru_solves_the_fp64_system(oracle, "bf16"))
               or _fails(lambda: pins.test_cg_ru_solves_the_fp64_system(oracle, "f32")))
+    assert caught
+
+
+SPMV_MUTANTS = {
+    # Algorithm 1 writes y(ai) instead of accumulating into it
+    "coo_overwrites": ("y[ai[e]] += av[e] * x[aj[e]];", "y[ai[e]] = av[e] * x[aj[e]];", 1),
+    # Algorithm 2 starts each row one entry late
+    "csr_skips_first_entry": ("for (int32_t j = irp[i]; j < irp[i + 1]; j++) sum += av[j] * x[aj[j]];",
+                              "for (int32_t j = irp[i] + 1; j < irp[i + 1]; j++) sum += av[j] * x[aj[j]];", 1),
+    # Algorithm 3's bounds check excludes column 0
+    "dia_bound_off_by_one": ("if (k >= 0 && k < n) sum += av[(int64_t)j * npad + i] * x[k];",
+                             "if (k > 0 && k < n) sum += av[(int64_t)j * npad + i] * x[k];", 1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SPMV_MUTANTS))
+def test_spmv_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
+    for c in pins.SMALL_CASES:   # the pins pass on the oracle as committed
+        pins.test_spmv_matches_dense_brute_force(oracle, c)
+    lib = _compile_mutant(tmp_path, *SPMV_MUTANTS[name])
+    _use(monkeypatch, lib)
+    caught = any(_fails(lambda c=c: pins.test_spmv_matches_dense_brute_force(oracle, c)) for c in pins.SMALL_CASES)
+    assert caught
+
+
+CG_MUTANTS = {
+    # beta formed the wrong way round
+    "beta_inverted": ("double beta = rho_new / rho;", "double beta = rho / rho_new;", 1),
+    # the solution advanced along q instead of p
+    "x_along_q": ("x[i] = x[i] + alpha * p[i];", "x[i] = x[i] + alpha * q[i];", 1),
+    # the residual updated with the wrong sign (also in the reliable-update solver's copy)
+    "residual_sign": ("r[i] = r[i] - alpha * q[i];", "r[i] = r[i] + alpha * q[i];", 2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CG_MUTANTS))
+def test_cg_pins_catch_planted_mistake(tmp_path, monkeypatch, name):
+    pins.test_cg_iterates_match_exact_rational_cg(oracle)   # passes on the oracle as committed
+    pins.test_cg_recovers_ones(oracle, 8, "csr")
+    lib = _compile_mutant(tmp_path, *CG_MUTANTS[name])
+    _use(monkeypatch, lib)
+    caught = (_fails(lambda: pins.test_cg_iterates_match_exact_rational_cg(oracle))
+              or _fails(lambda: pins.test_cg_recovers_ones(oracle, 8, "csr")))
     assert caught
