@@ -134,7 +134,6 @@ constexpr int OFF_MU = 0, OFF_SD = NF, OFF_LO = 2 * NF, OFF_HI = 3 * NF, OFF_W1 
               OFF_B2 = OFF_W2 + NH * NH, OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NC * NH,
               NPARAM = OFF_B3 + NC;
 static_assert(NPARAM == kSelectorParams, "parameter layout");
-constexpr int NTRAIN = NPARAM - OFF_W1;   // trained parameters (everything after mu, sd, lo, hi)
 
 // Output k (0-based) of SplitMix64 seeded with `seed` (Steele, Lea, Flood, "Fast splittable
 // pseudorandom number generators", OOPSLA 2014): the state advances by the golden gamma
