@@ -63,3 +63,30 @@ def test_family_recipe(seed, backend):
         assert 10 <= lens.mean() <= 20
     else:
         assert np.all(lens == 32) and np.all(c // 32 == r // 32)
+
+
+@pytest.mark.parametrize("g,seed", [(5, 1), (8, 3)])
+def test_perturbed_stencil_recipe(g, seed):
+    """The perturbed SPD stencil as stated: the 27-point pattern, off-diagonals -(1 + 0.1 u)
+    with u in [0, 1) and the same value for (i, j) and (j, i), the diagonal the left-to-right
+    sum of |off| plus 1 (so every row sums to exactly 1 up to that sum's rounding), values that
+    FP32 does round, and a symmetric positive definite matrix (Gershgorin)."""
+    n = g ** 3
+    r0, c0, _ = synth.stencil27(g)
+    r, c, v = synth.stencil27_perturbed(g, seed)
+    assert np.array_equal(r, r0) and np.array_equal(c, c0)
+    D = np.zeros((n, n))
+    D[r, c] = v
+    off = r != c
+    assert np.all((v[off] <= -1.0) & (v[off] > -1.1))
+    assert np.array_equal(D, D.T)
+    for i in range(n):
+        row = np.nonzero(r == i)[0]
+        s = 0.0
+        for e in row:   # left to right in column order, off-diagonals only
+            if c[e] != i:
+                s += abs(v[e])
+        assert D[i, i] == s + 1.0
+    assert np.allclose(D.sum(axis=1), 1.0, rtol=0, atol=1e-12)
+    assert np.any(v.astype(np.float32).astype(np.float64) != v)
+    assert np.linalg.eigvalsh(D).min() >= 1.0 - 1e-9
